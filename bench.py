@@ -1,0 +1,467 @@
+#!/usr/bin/env python3
+"""Benchmark: exact short-pattern search throughput on GB300.
+
+Workload (default ``sweep``, the pattern-length sweep): three synthetic texts of
+n = 256 MiB each — sigma=4 uniform DNA-like, sigma=20 uniform protein-like,
+sigma=64 natural-language-like (Zipf s=1.1 with a 15% space symbol) — and for
+each text 100 patterns per m in {2, 4, 8, 16, 32}, half copied from random text
+offsets and half drawn i.i.d. from the text's symbol distribution.  One step
+searches every (text, pattern) pair: 1500 searches, 402.7 GB of text.  Each
+search produces its count and all sorted uint64 start positions.
+
+Metric: text GB/s (bytes of text scanned / second), device-timed with the
+texts resident in HBM.  ``e2e`` is the same metric through the public C entry
+point that takes HOST buffers (epsm_search_host), with the texts' host->device
+copies and the positions' device->host copies inside the timed region.
+
+``--impl reference`` times the CPU oracle (brute-force scan) on the host cores
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+GiB = 1 << 30
+MiB = 1 << 20
+METRIC = "text GB/s (pattern-length sweep, m=2..32)"
+UNIT = "GB/s"
+KINDS = ("dna", "protein", "nl64")
+MS = (2, 4, 8, 16, 32)
+PATS_PER_M = 100
+TEXT_N = 256 * MiB
+L2_BYTES = 129 * 10**6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="epsm", choices=["epsm", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--patterns", type=int, default=PATS_PER_M,
+                    help="patterns per (text, m); the workload uses 100")
+    ap.add_argument("--case", default=None,
+                    help="KIND:M[:VARIANT[:N]] — time one search of an N-byte text "
+                         "(default 256 MiB) and exit (the small case used for ncu captures)")
+    ap.add_argument("--reps", type=int, default=3)
+    return ap.parse_args()
+
+
+def run_case(args):
+    """One search configuration, timed with CUDA events (for profiling)."""
+    import torch
+    import gen
+    import paper_1209_6449_gb300 as epsm
+    parts = args.case.split(":")
+    kind, m = parts[0], int(parts[1])
+    variant = int(parts[2]) if len(parts) > 2 else 0
+    n = int(parts[3]) if len(parts) > 3 else TEXT_N
+    ctx = epsm.Context(0)
+    t = torch.empty(n, dtype=torch.uint8, device="cuda")
+    gen.TextSpec(kind, 0).device(n, t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    pat = gen.planted_patterns(gen.TextSpec(kind, 0), n, m, 1)[0]
+    cap = n // 3
+    out = torch.empty(cap, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    times = []
+    for _ in range(args.reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.search_async(t, pat, out, cap, cnt, variant=variant)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    st = ctx.sync()
+    print(json.dumps({"case": args.case, "n": n, "count": int(cnt.item()), "status": st,
+                      "ms": [round(x, 4) for x in times],
+                      "gbs_best": round(n / min(times) / 1e6, 1)}), flush=True)
+    ctx.close()
+    return 0 if st == 0 else 1
+
+
+def workload_patterns(npat):
+    import gen
+    out = []
+    for kind in KINDS:
+        spec = gen.TextSpec(kind, 0)
+        for m in MS:
+            for p in gen.mixed_patterns(spec, TEXT_N, m, npat):
+                out.append((kind, m, p))
+    return out
+
+
+def config(npat, ngpus):
+    return {"workload": "pattern-length sweep: 3 texts x 256 MiB (sigma 4 DNA-like, sigma 20 "
+                        "protein-like, sigma 64 Zipf natural-language-like), m in {2,4,8,16,32}, "
+                        f"{npat} patterns per (text, m), half planted half i.i.d.",
+            "text_bytes": TEXT_N, "texts": list(KINDS), "m": list(MS),
+            "patterns_per_text_and_m": npat, "searches_per_step": len(KINDS) * len(MS) * npat,
+            "l2": "inputs larger than L2 (256 MiB text vs 129 MB L2); no flush",
+            "parallelism": f"replicas x{ngpus}" if ngpus > 1 else "single GPU"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [l for (t, l) in self.lines if t0 - 0.15 <= t <= t1 + 0.15] or [l for _, l in self.lines]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm / CPU baseline: the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_sample(budget_s, texts_host):
+    """Time the oracle on a bounded sample: the first 8 MiB of each text, two
+    patterns per (text, m), repeated until about budget_s seconds."""
+    import gen
+    import oracle
+    cores = os.cpu_count() or 1
+    sample_n = 8 * MiB
+    jobs = []
+    for kind in KINDS:
+        spec = gen.TextSpec(kind, 0)
+        t = texts_host[kind][:sample_n] if texts_host else spec.host(sample_n)
+        for m in MS:
+            for p in gen.mixed_patterns(spec, TEXT_N, m, 2):
+                jobs.append((t, p))
+    scanned, t0 = 0, time.perf_counter()
+    rounds = 0
+    while True:
+        for t, p in jobs:
+            oracle.count(t, p, threads=cores)
+            scanned += t.size
+        rounds += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(scanned / dt / 1e9, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{rounds} round(s) of {len(jobs)} searches (3 texts x 5 m x 2 patterns) "
+                      f"over the first 8 MiB of each text, brute-force C oracle on {cores} threads"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import gen
+    import oracle
+    cores = os.cpu_count() or 1
+    sample_n = 4 * MiB
+    jobs = []
+    for kind in KINDS:
+        spec = gen.TextSpec(kind, 0)
+        t = spec.host(sample_n)
+        for m in MS:
+            p = gen.mixed_patterns(spec, TEXT_N, m, 2)[0]
+            jobs.append((t, p))
+
+    def step():
+        tot = 0
+        for t, p in jobs:
+            oracle.count(t, p, threads=cores)
+            tot += t.size
+        return tot
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    tot = 0
+    for _ in range(args.steps):
+        tot += step()
+    dt = time.perf_counter() - t0
+    v = tot / dt / 1e9
+    sample = (f"each step: 15 searches (3 texts x 5 m x 1 pattern) over the first 4 MiB of each "
+              f"text, brute-force C oracle on {cores} threads")
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": config(args.patterns, args.gpus),
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# roofline inputs
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1209_6449_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.case:
+        return run_case(args)
+
+    import torch
+    import gen
+    import paper_1209_6449_gb300 as epsm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device(f"cuda:{local if world > 1 else 0}")
+    ctx = epsm.Context(dev.index)
+    stream = torch.cuda.current_stream()
+
+    # texts resident in HBM, generated on the device
+    texts = {}
+    for kind in KINDS:
+        t = torch.empty(TEXT_N, dtype=torch.uint8, device=dev)
+        gen.TextSpec(kind, 0).device(TEXT_N, t.data_ptr(), stream.cuda_stream)
+        texts[kind] = t
+    pats = workload_patterns(args.patterns)
+    nsearch = len(pats)
+    cap = TEXT_N // 8
+    out = torch.empty(cap, dtype=torch.int64, device=dev)
+    counts = torch.zeros(nsearch, dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        for i, (kind, m, p) in enumerate(pats):
+            ctx.search_async(texts[kind], p, out, cap, counts[i:i + 1], stream=stream)
+
+    launches0 = ctx.launch_count
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = ctx.sync()
+    if st != 0:
+        raise SystemExit(f"device status {st} after warm-up")
+    occ = counts.cpu().numpy()
+    assert int(occ.max()) <= cap, "output capacity exceeded"
+
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches_before = ctx.launch_count
+    t_wall0 = time.time()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if dist:
+        dist.barrier()
+    launches = ctx.launch_count - launches_before
+    elapsed_ms = e0.elapsed_time(e1)
+    clocks.stop()
+    st = ctx.sync()
+    if st != 0:
+        raise SystemExit(f"device status {st} after timed region")
+    if dist:
+        tt = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+
+    bytes_per_step = nsearch * TEXT_N
+    value = world * bytes_per_step * args.steps / (elapsed_ms / 1e3) / 1e9
+    occ_total = int(occ.sum())
+    # roofline of the scan kernel: algorithmic bytes = text read + 8 B per
+    # written position + 8 B count, per launch; duration = timed region / launches
+    alg_bytes_per_launch = (bytes_per_step + 8 * occ_total + 8 * nsearch) / nsearch
+    per_launch_s = elapsed_ms / 1e3 / max(launches, 1)
+    achieved = alg_bytes_per_launch / per_launch_s / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = profiled_traffic()
+
+    e2e = None
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = oracle_sample(12.0, None)
+    if not args.no_e2e:
+        e2e = run_e2e(ctx, pats, args, torch, dev, dist)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(elapsed_ms / args.steps, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+                "config": config(args.patterns, world),
+                "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                             "unit": "GB/s", "frac": round(achieved / peak, 4),
+                             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                             "kernel": "scan_kernel (all variants; algorithmic bytes = n + 8*occ + 8 per launch)",
+                             "traffic": traffic.get("bytes_per_launch") if traffic else None},
+                "cpu_baseline": cpu,
+                "e2e": e2e,
+                "gpu_launches": launches,
+                "clocks": clocks.summary(t_wall0, t_wall1),
+                "occurrences_per_step": occ_total}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+def run_e2e(ctx, pats, args, torch, dev, dist):
+    """Same workload through epsm_search_host: host texts in, host positions out."""
+    import gen
+    from paper_1209_6449_gb300 import epsm_search_host
+    hosts = {}
+    for kind in KINDS:
+        h = torch.empty(TEXT_N, dtype=torch.uint8, pin_memory=True)
+        h.numpy()[:] = gen.TextSpec(kind, 0).host(TEXT_N)
+        hosts[kind] = h.numpy()
+    groups = {k: [p for (kk, m, p) in pats if kk == k] for k in KINDS}
+    # capacity per call: the largest per-text total seen on the device path
+    caps = {}
+    for k in KINDS:
+        st, offs = epsm_search_host(ctx.handle, hosts[k], groups[k],
+                                    np.zeros(0, dtype=np.uint64))
+        caps[k] = int(offs[-1])
+    cap = max(caps.values())
+    pos_host = torch.empty(max(cap, 1), dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    d2h = 0
+
+    def step():
+        nonlocal d2h
+        d2h = 0
+        for k in KINDS:
+            st, offs = epsm_search_host(ctx.handle, hosts[k], groups[k], pos_host[:cap])
+            if st != 0:
+                raise SystemExit(f"epsm_search_host status {st}")
+            d2h += int(offs[-1]) * 8 + offs.size * 8
+    for _ in range(max(1, args.warmup)):
+        step()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([dt], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt = float(tt.item())
+    world = dist.get_world_size() if dist else 1
+    scanned = len(pats) * TEXT_N * args.steps * world
+    h2d = len(KINDS) * TEXT_N + sum(len(p) for (_, _, p) in pats)
+    return {"value": round(scanned / dt / 1e9, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "api": "epsm_search_host (one call per text, "
+                                              "pinned host buffers)"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,156 @@
+/*
+ * epsm.h — C ABI of the GB300 exact short-pattern matching library.
+ *
+ * Operation (Section 1 and Section 2 of Faro & Kulekci, "Fast Packed String
+ * Matching for Short Patterns"): given a text t[0..n-1] and a pattern
+ * p[0..m-1] of bytes, report ALL start positions s with 0 <= s <= n-m and
+ * t[s+i] == p[i] for every i < m.  Overlapping occurrences are all reported,
+ * bytes compare as unsigned values, and positions are 0-based uint64 in
+ * ascending order.  The library implements the three length regimes of
+ * Section 3 (a packed window compare for very short patterns, a first-bytes
+ * filter plus in-register verify for short patterns, an aligned-block
+ * fingerprint filter plus verify for medium patterns) as sm_103a kernels.
+ *
+ * Conventions for every entry point:
+ *   - 1 <= m <= EPSM_MAX_M (32); m == 0 or m > 32 returns EPSM_ERR_ARG.
+ *   - m > n is not an error: the count is 0.
+ *   - Inputs are never modified.  Buffers named "device" must be device
+ *     memory of the context's device (or managed memory); buffers named "host"
+ *     are ordinary host memory (pinned memory makes copies faster).
+ *   - If the number of occurrences exceeds `capacity`, the first `capacity`
+ *     positions are written, the true count is reported, and the call returns
+ *     EPSM_ERR_CAPACITY.  capacity == 0 (positions may then be NULL) counts
+ *     only.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL is the CUDA default
+ *     stream).  A context is not thread-safe: use one context per host
+ *     thread.  Calls on one context that use different streams are ordered
+ *     by the context (each call waits for the previous one's scratch use).
+ *   - A bounded device-side wait that gives up makes the call return
+ *     EPSM_ERR_TIMEOUT; the context stays usable.
+ *   - The library allocates device scratch inside the context only (tile
+ *     status words, counters, staging buffers); it never frees caller memory.
+ */
+#ifndef EPSM_H
+#define EPSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EPSM_MAX_M 32u
+
+typedef struct epsm_ctx epsm_ctx;
+
+typedef enum {
+    EPSM_OK = 0,
+    EPSM_ERR_ARG = 1,       /* bad argument (NULL pointer, m out of range, ...) */
+    EPSM_ERR_CAPACITY = 2,  /* more occurrences than capacity; true count reported */
+    EPSM_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+    EPSM_ERR_NOMEM = 4,     /* scratch or staging allocation failed */
+    EPSM_ERR_TIMEOUT = 5    /* a bounded device wait gave up; results are invalid */
+} epsm_status;
+
+/* Search variants (the length regimes of Section 3 mapped to GPU kernels).
+ * EPSM_VARIANT_AUTO lets the context's tuning table choose by m. */
+typedef enum {
+    EPSM_VARIANT_AUTO = 0,
+    EPSM_VARIANT_DIRECT = 1,   /* packed window compare, 1 <= m <= 4   (Section 3.2, EPSMa) */
+    EPSM_VARIANT_PREFIX4 = 2,  /* 4-byte first-bytes filter + verify, 4 <= m <= 15 (Section 3.3, EPSMb) */
+    EPSM_VARIANT_PREFIX8 = 3,  /* 8-byte first-bytes filter + verify, 8 <= m <= 15 (Section 3.3, EPSMb with m' = 8) */
+    EPSM_VARIANT_BLOCK8 = 4    /* aligned 8-byte block fingerprint + verify, 15 <= m <= 32 (Section 3.4, EPSMc) */
+} epsm_variant;
+
+/* Create a context on CUDA device `device`.  `flags` is reserved (pass 0).
+ * On success *out owns a stream and lazily grown device scratch. */
+epsm_status epsm_create(epsm_ctx **out, int device, uint64_t flags);
+
+/* Release the context, its stream and its scratch.  NULL is accepted. */
+epsm_status epsm_destroy(epsm_ctx *ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char *epsm_status_str(epsm_status s);
+
+/* Last CUDA error string seen by the context (static or context storage). */
+const char *epsm_last_error(epsm_ctx *ctx);
+
+/* Single search, synchronous (Section 1 problem; Section 3 procedures).
+ *   text      device, n bytes (any alignment), caller-owned
+ *   pattern   host, m bytes, copied before the call returns
+ *   positions device, room for `capacity` uint64, caller-owned (NULL iff capacity == 0)
+ *   count     host: receives the true number of occurrences
+ * Returns after the result is complete. */
+epsm_status epsm_search(epsm_ctx *ctx, const uint8_t *text, uint64_t n,
+                        const uint8_t *pattern, uint32_t m,
+                        uint64_t *positions, uint64_t capacity,
+                        uint64_t *count, void *stream);
+
+/* Single search, asynchronous: like epsm_search, but `count_dev` is DEVICE
+ * memory that receives the true count when the enqueued work completes, and the
+ * call returns once the work is enqueued.  Capacity overflow and device wait
+ * timeouts are reported by the next epsm_sync on the context. */
+epsm_status epsm_search_async(epsm_ctx *ctx, const uint8_t *text, uint64_t n,
+                              const uint8_t *pattern, uint32_t m,
+                              uint64_t *positions, uint64_t capacity,
+                              uint64_t *count_dev, void *stream);
+
+/* Same as epsm_search_async with an explicit variant (EPSM_VARIANT_AUTO picks
+ * by the tuning table).  A variant that does not cover m returns EPSM_ERR_ARG. */
+epsm_status epsm_search_variant(epsm_ctx *ctx, int variant, const uint8_t *text, uint64_t n,
+                                const uint8_t *pattern, uint32_t m,
+                                uint64_t *positions, uint64_t capacity,
+                                uint64_t *count_dev, void *stream);
+
+/* Wait for the context's outstanding work on `stream` (NULL = default stream)
+ * and report device-side errors raised since the last sync: EPSM_ERR_TIMEOUT
+ * if a bounded wait gave up, EPSM_ERR_CAPACITY if an asynchronous search found
+ * more occurrences than its capacity, EPSM_ERR_CUDA on a CUDA error. */
+epsm_status epsm_sync(epsm_ctx *ctx, void *stream);
+
+/* Batched search over `npairs` independent (text, pattern) pairs of uneven n
+ * and m, in one persistent launch (north of the paper: each pair is one
+ * Section 1 problem).
+ *   texts      host array of npairs DEVICE text pointers
+ *   ns         host array of npairs text lengths
+ *   patterns   host array of npairs HOST pattern pointers
+ *   ms         host array of npairs pattern lengths (each 1..32)
+ *   positions  device pool of `capacity` uint64; pair i's sorted positions are
+ *              written at [offsets[i], offsets[i+1])
+ *   offsets    host array of npairs+1 entries (offsets[npairs] = total count)
+ * Synchronous.  Pool overflow returns EPSM_ERR_CAPACITY with offsets filled. */
+epsm_status epsm_search_batch(epsm_ctx *ctx, uint32_t npairs,
+                              const uint8_t *const *texts, const uint64_t *ns,
+                              const uint8_t *const *patterns, const uint32_t *ms,
+                              uint64_t *positions, uint64_t capacity,
+                              uint64_t *offsets, void *stream);
+
+/* End-to-end search from HOST memory: copies the text to the device, searches
+ * it for `npat` patterns in one batched launch, and copies the results back.
+ *   text_host      host, n bytes
+ *   patterns_host  host, concatenation of the npat patterns
+ *   ms             host, npat pattern lengths (each 1..32)
+ *   positions_host host, room for `capacity` uint64
+ *   offsets_host   host, npat+1 entries (pattern k's positions are at
+ *                  [offsets[k], offsets[k+1]); offsets[npat] = total)
+ * Synchronous. */
+epsm_status epsm_search_host(epsm_ctx *ctx, const uint8_t *text_host, uint64_t n,
+                             const uint8_t *patterns_host, const uint32_t *ms, uint32_t npat,
+                             uint64_t *positions_host, uint64_t capacity,
+                             uint64_t *offsets_host);
+
+/* Variant the context uses for pattern length m under EPSM_VARIANT_AUTO. */
+int epsm_variant_for(epsm_ctx *ctx, uint32_t m);
+
+/* Override the automatic variant for pattern length m (1..32); `variant` must
+ * cover m.  Used by the autotuner to install its table. */
+epsm_status epsm_set_variant(epsm_ctx *ctx, uint32_t m, int variant);
+
+/* Number of kernel launches the context has issued (all entry points). */
+uint64_t epsm_launch_count(epsm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPSM_H */

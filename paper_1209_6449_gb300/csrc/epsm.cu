@@ -1,0 +1,577 @@
+// Host runtime and C ABI of the exact short-pattern matching library (see
+// include/epsm.h for the contract of every entry point).
+//
+// The runtime validates arguments, picks the kernel variant for the pattern
+// length (Section 3: the EPSM dispatcher chooses its procedure by m), packs
+// the pattern, sizes the persistent grid from the SM count and the kernel's
+// occupancy, manages the context's device scratch (look-back status words,
+// tile ticket, error word) and enqueues the kernels.  Every step of the
+// search itself runs in the kernels of epsm_kernels.cuh.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "epsm.h"
+#include "epsm_kernels.cuh"
+#include "epsm_stream.cuh"
+
+using namespace epsm;
+
+#define EPSM_API extern "C" __attribute__((visibility("default")))
+
+namespace {
+
+constexpr int kDefaultU = 4;                          // chunks per lane per tile
+constexpr uint64_t kTileBytes = (uint64_t)kThreads * kDefaultU * 16u;  // 16 KiB
+constexpr uint32_t kTagMax = (1u << 22) - 1u;
+
+int default_variant(uint32_t m) {
+    if (m <= 3) return V_DIRECT;
+    if (m <= 7) return V_PREFIX4;
+    if (m <= 14) return V_PREFIX8;
+    return V_BLOCK8;
+}
+
+bool variant_covers(int v, uint32_t m) {
+    switch (v) {
+        case V_DIRECT: return m >= 1 && m <= 4;
+        case V_PREFIX4: return m >= 4 && m <= 15;
+        case V_PREFIX8: return m >= 8 && m <= 15;
+        case V_BLOCK8: return m >= 15 && m <= 32;
+        default: return false;
+    }
+}
+
+int variant_offset(int v) { return v == V_BLOCK8 ? -7 : 0; }
+
+// Tiles needed for a job: tile t covers starts [t*T + OFF, (t+1)*T + OFF).
+uint64_t tiles_for(uint64_t delta, uint64_t n, uint32_t m, int v) {
+    if (n < m || n == 0) return 0;
+    int64_t pmax = (int64_t)(delta + n - m);
+    return (uint64_t)((pmax - variant_offset(v)) / (int64_t)kTileBytes) + 1u;
+}
+
+Pattern pack_pattern(const uint8_t *p, uint32_t m) {
+    Pattern pat;
+    memset(&pat, 0, sizeof(pat));
+    uint8_t bytes[32];
+    memset(bytes, 0, sizeof(bytes));
+    memcpy(bytes, p, m);
+    for (int i = 0; i < 8; ++i)
+        pat.w[i] = (uint32_t)bytes[4 * i] | ((uint32_t)bytes[4 * i + 1] << 8) |
+                   ((uint32_t)bytes[4 * i + 2] << 16) | ((uint32_t)bytes[4 * i + 3] << 24);
+    pat.m = m;
+    return pat;
+}
+
+SearchJob make_job(const uint8_t *text, uint64_t n, const Pattern &pat) {
+    SearchJob J;
+    uintptr_t t = reinterpret_cast<uintptr_t>(text);
+    J.base = reinterpret_cast<const uint8_t *>(t & ~(uintptr_t)15);
+    J.delta = (uint64_t)(t & 15);
+    J.lim = J.delta + n;
+    J.pmax = (int64_t)(J.delta + n) - (int64_t)pat.m;
+    J.pat = pat;
+    return J;
+}
+
+std::mutex g_occ_mu;
+std::unordered_map<const void *, int> g_occ;
+
+int blocks_per_sm(const void *fn) {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    auto it = g_occ.find(fn);
+    if (it != g_occ.end()) return it->second;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kThreads, 0) != cudaSuccess || b < 1) b = 1;
+    g_occ[fn] = b;
+    return b;
+}
+
+}  // namespace
+
+struct epsm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sms = 0;
+    DevMisc *misc = nullptr;     // device
+    DevMisc *hmisc = nullptr;    // pinned host mirror
+    uint64_t *status = nullptr;  // look-back status words
+    uint64_t status_cap = 0;
+    uint32_t epoch = 0;
+    cudaEvent_t ev = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool have_ev = false;
+    int variant[EPSM_MAX_M + 1];
+    uint64_t launches = 0;
+    char errbuf[256];
+    // batch staging
+    BatchPair *hpairs = nullptr;
+    BatchPair *dpairs = nullptr;
+    uint32_t pairs_cap = 0;
+    uint64_t *hoffsets = nullptr;
+    uint64_t *doffsets = nullptr;
+    uint32_t offsets_cap = 0;
+    // streaming-kernel scratch
+    uint32_t *seg_count = nullptr;
+    uint16_t *seg_mask = nullptr;
+    uint64_t seg_cap = 0;
+    // host end-to-end staging
+    uint8_t *dtext = nullptr;
+    uint64_t dtext_cap = 0;
+    uint64_t *dpos = nullptr;
+    uint64_t dpos_cap = 0;
+};
+
+namespace {
+
+epsm_status cuda_fail(epsm_ctx *c, cudaError_t e, const char *what) {
+    if (c) snprintf(c->errbuf, sizeof(c->errbuf), "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? EPSM_ERR_NOMEM : EPSM_ERR_CUDA;
+}
+
+#define CK(call)                                               \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+// NULL is the CUDA default stream, as for every CUDA library call.
+cudaStream_t pick_stream(epsm_ctx *c, void *s) {
+    (void)c;
+    return (cudaStream_t)s;
+}
+
+// Orders this call after the previous call of the context when it used
+// another stream (the scratch words are shared).
+epsm_status order_after_previous(epsm_ctx *c, cudaStream_t s) {
+    if (c->have_ev && c->last_stream != s) CK(cudaStreamWaitEvent(s, c->ev, 0));
+    return EPSM_OK;
+}
+
+epsm_status mark_done(epsm_ctx *c, cudaStream_t s) {
+    CK(cudaEventRecord(c->ev, s));
+    c->have_ev = true;
+    c->last_stream = s;
+    return EPSM_OK;
+}
+
+epsm_status ensure_status(epsm_ctx *c, uint64_t ntiles, cudaStream_t s) {
+    if (ntiles <= c->status_cap) return EPSM_OK;
+    uint64_t cap = std::max<uint64_t>(ntiles, c->status_cap * 2);
+    CK(cudaStreamSynchronize(s));
+    if (c->status) CK(cudaFree(c->status));
+    c->status = nullptr;
+    c->status_cap = 0;
+    CK(cudaMalloc(&c->status, cap * kStatusStride * sizeof(uint64_t)));
+    CK(cudaMemsetAsync(c->status, 0, cap * kStatusStride * sizeof(uint64_t), s));
+    c->status_cap = cap;
+    return EPSM_OK;
+}
+
+// Scratch of the streaming kernel: one count per 2 KiB segment and 128 chunk
+// masks (256 B) per segment, i.e. n/512 + n/8 bytes; status words for the blocks.
+epsm_status ensure_stream_scratch(epsm_ctx *c, uint64_t nstages, cudaStream_t s) {
+    epsm_status st = ensure_status(c, (uint64_t)std::max(c->sms, 1) * stream::kMaxBlocksPerSm, s);
+    if (st != EPSM_OK) return st;
+    const uint64_t nseg = nstages * stream::kConsumerWarps;
+    if (nseg <= c->seg_cap) return EPSM_OK;
+    uint64_t cap = std::max<uint64_t>(nseg, c->seg_cap * 2);
+    CK(cudaStreamSynchronize(s));
+    if (c->seg_count) CK(cudaFree(c->seg_count));
+    if (c->seg_mask) CK(cudaFree(c->seg_mask));
+    c->seg_count = nullptr;
+    c->seg_mask = nullptr;
+    c->seg_cap = 0;
+    CK(cudaMalloc(&c->seg_count, cap * sizeof(uint32_t)));
+    CK(cudaMalloc(&c->seg_mask, cap * stream::kSegChunks * sizeof(uint16_t)));
+    c->seg_cap = cap;
+    return EPSM_OK;
+}
+
+epsm_status next_tag(epsm_ctx *c, cudaStream_t s, uint32_t *tag) {
+    c->epoch = c->epoch % kTagMax + 1u;
+    if (c->epoch == 1u && c->status_cap) {
+        // tags wrapped: clear every status word so that no stale word matches
+        CK(cudaMemsetAsync(c->status, 0, c->status_cap * kStatusStride * sizeof(uint64_t), s));
+    }
+    *tag = c->epoch;
+    return EPSM_OK;
+}
+
+// Single searches run the cooperative streaming kernel (epsm_stream.cuh): one
+// block per SM, all co-resident.
+template <int V, int MP>
+cudaError_t launch_stream_t(epsm_ctx *c, const stream::StreamParams &p, cudaStream_t s) {
+    static int per_sm = 0;  // co-resident blocks per SM (cooperative launch bound)
+    const size_t smem = sizeof(stream::StreamSmem);
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(stream_kernel<V, MP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stream_kernel<V, MP>,
+                                                          stream::kThreadsStream, smem);
+        if (e != cudaSuccess) return e;
+        per_sm = std::max(1, std::min(b, stream::kMaxBlocksPerSm));
+    }
+    const unsigned grid = (unsigned)std::min<uint64_t>(std::max<uint64_t>(p.nstages, 1u),
+                                                       (uint64_t)c->sms * per_sm);
+    void *args[] = {(void *)&p};
+    return cudaLaunchCooperativeKernel((const void *)stream_kernel<V, MP>, dim3(grid),
+                                       dim3(stream::kThreadsStream), args, smem, s);
+}
+
+cudaError_t launch_stream(epsm_ctx *c, int v, uint32_t m, const stream::StreamParams &p,
+                          cudaStream_t s) {
+    switch (v) {
+        case V_DIRECT:
+            switch (m) {
+                case 1: return launch_stream_t<V_DIRECT, 1>(c, p, s);
+                case 2: return launch_stream_t<V_DIRECT, 2>(c, p, s);
+                case 3: return launch_stream_t<V_DIRECT, 3>(c, p, s);
+                default: return launch_stream_t<V_DIRECT, 4>(c, p, s);
+            }
+        case V_PREFIX4: return launch_stream_t<V_PREFIX4, 4>(c, p, s);
+        case V_PREFIX8: return launch_stream_t<V_PREFIX8, 8>(c, p, s);
+        default: return launch_stream_t<V_BLOCK8, 8>(c, p, s);
+    }
+}
+
+// Stages of 16 KiB needed for a job: stage k covers starts [16K*k + OFF, 16K*(k+1) + OFF).
+uint64_t stages_for(uint64_t delta, uint64_t n, uint32_t m, int v) {
+    if (n < m || n == 0) return 0;
+    int64_t pmax = (int64_t)(delta + n - m);
+    return (uint64_t)((pmax - variant_offset(v)) / (int64_t)stream::kStageBytes) + 1u;
+}
+
+epsm_status search_async_impl(epsm_ctx *c, int variant, const uint8_t *text, uint64_t n,
+                              const uint8_t *pattern, uint32_t m, uint64_t *positions,
+                              uint64_t capacity, uint64_t *count_dev, void *stream,
+                              int64_t pos_bias) {
+    if (!c || !pattern || !count_dev) return EPSM_ERR_ARG;
+    if (m == 0 || m > EPSM_MAX_M) return EPSM_ERR_ARG;
+    if (n > 0 && !text) return EPSM_ERR_ARG;
+    if (capacity > 0 && !positions) return EPSM_ERR_ARG;
+    int v = variant == EPSM_VARIANT_AUTO ? c->variant[m] : variant;
+    if (!variant_covers(v, m)) return EPSM_ERR_ARG;
+    cudaStream_t s = pick_stream(c, stream);
+    epsm_status st = order_after_previous(c, s);
+    if (st != EPSM_OK) return st;
+    if (n < m) {
+        CK(cudaMemsetAsync(count_dev, 0, sizeof(uint64_t), s));
+        return mark_done(c, s);
+    }
+    stream::StreamParams p;
+    memset(&p, 0, sizeof(p));
+    p.job = make_job(text, n, pack_pattern(pattern, m));
+    p.nstages = stages_for(p.job.delta, n, m, v);
+    p.chunk_full0 = (p.job.delta + 15u) / 16u;
+    p.chunk_full1 = p.job.lim / 16u;
+    p.emit = capacity > 0 ? 1 : 0;
+    (void)pos_bias;
+    if ((st = ensure_stream_scratch(c, p.nstages, s)) != EPSM_OK) return st;
+    uint32_t tag = 0;
+    if ((st = next_tag(c, s, &tag)) != EPSM_OK) return st;
+    p.positions = positions;
+    p.capacity = capacity;
+    p.count_out = count_dev;
+    p.seg_count = c->seg_count;
+    p.seg_mask = c->seg_mask;
+    p.cta_status = c->status;
+    p.err = &c->misc->err;
+    p.tag = tag;
+    CK(launch_stream(c, v, m, p, s));
+    c->launches += 1;
+    return mark_done(c, s);
+}
+
+// Reads the device scratch words after the stream drained; clears the error word.
+epsm_status read_misc(epsm_ctx *c, cudaStream_t s, uint32_t *err) {
+    CK(cudaMemcpyAsync(c->hmisc, c->misc, sizeof(DevMisc), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *err = c->hmisc->err;
+    if (*err) {
+        CK(cudaMemsetAsync(&c->misc->err, 0, sizeof(uint32_t), s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return EPSM_OK;
+}
+
+template <typename T>
+epsm_status grow_pinned(epsm_ctx *c, T **h, T **d, uint32_t *cap, uint32_t need) {
+    if (need <= *cap) return EPSM_OK;
+    uint32_t nc = std::max<uint32_t>(need, *cap * 2);
+    CK(cudaDeviceSynchronize());
+    if (*h) CK(cudaFreeHost(*h));
+    if (*d) CK(cudaFree(*d));
+    *h = nullptr;
+    *d = nullptr;
+    *cap = 0;
+    CK(cudaMallocHost((void **)h, sizeof(T) * nc));
+    CK(cudaMalloc((void **)d, sizeof(T) * nc));
+    *cap = nc;
+    return EPSM_OK;
+}
+
+epsm_status batch_impl(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts,
+                       const uint64_t *ns, const uint8_t *const *patterns, const uint32_t *ms,
+                       uint64_t *positions, uint64_t capacity, uint64_t *offsets,
+                       cudaStream_t s) {
+    epsm_status st;
+    if ((st = grow_pinned(c, &c->hpairs, &c->dpairs, &c->pairs_cap, npairs)) != EPSM_OK) return st;
+    if ((st = grow_pinned(c, &c->hoffsets, &c->doffsets, &c->offsets_cap, npairs + 1)) != EPSM_OK)
+        return st;
+    uint64_t tile0 = 0;
+    std::vector<uint8_t> empty(npairs, 0);
+    for (uint32_t i = 0; i < npairs; ++i) {
+        BatchPair &bp = c->hpairs[i];
+        memset(&bp, 0, sizeof(bp));
+        int v = c->variant[ms[i]];
+        bp.job = make_job(texts[i], ns[i], pack_pattern(patterns[i], ms[i]));
+        bp.variant = (uint32_t)v;
+        bp.tile0 = tile0;
+        uint64_t nt = tiles_for(bp.job.delta, ns[i], ms[i], v);
+        empty[i] = nt == 0;
+        tile0 += nt;
+    }
+    const uint64_t ntiles = tile0;
+    if ((st = order_after_previous(c, s)) != EPSM_OK) return st;
+    if (ntiles > 0) {
+        if ((st = ensure_status(c, ntiles, s)) != EPSM_OK) return st;
+        uint32_t tag = 0;
+        if ((st = next_tag(c, s, &tag)) != EPSM_OK) return st;
+        CK(cudaMemcpyAsync(c->dpairs, c->hpairs, sizeof(BatchPair) * npairs,
+                           cudaMemcpyHostToDevice, s));
+        BatchParams p;
+        memset(&p, 0, sizeof(p));
+        p.pairs = c->dpairs;
+        p.npairs = npairs;
+        p.ntiles = ntiles;
+        p.out.positions = positions;
+        p.out.capacity = capacity;
+        p.out.status = c->status;
+        p.out.err = &c->misc->err;
+        p.out.tag = tag;
+        p.offsets = c->doffsets;
+        p.misc = c->misc;
+        const void *fn = (const void *)batch_kernel<kDefaultU>;
+        uint64_t grid = std::min<uint64_t>(ntiles, (uint64_t)c->sms * blocks_per_sm(fn));
+        batch_kernel<kDefaultU><<<(unsigned)grid, kThreads, 0, s>>>(p);
+        CK(cudaGetLastError());
+        c->launches += 1;
+        CK(cudaMemcpyAsync(c->hoffsets, c->doffsets, sizeof(uint64_t) * (npairs + 1),
+                           cudaMemcpyDeviceToHost, s));
+    }
+    if ((st = mark_done(c, s)) != EPSM_OK) return st;
+    uint32_t err = 0;
+    if (ntiles > 0) {
+        if ((st = read_misc(c, s, &err)) != EPSM_OK) return st;
+    }
+    // Pairs without tiles (n < m) own an empty range at the next pair's offset.
+    offsets[npairs] = ntiles > 0 ? c->hoffsets[npairs] : 0;
+    for (uint32_t i = npairs; i-- > 0;) offsets[i] = empty[i] ? offsets[i + 1] : c->hoffsets[i];
+    if (err & kErrTimeout) return EPSM_ERR_TIMEOUT;
+    return offsets[npairs] > capacity ? EPSM_ERR_CAPACITY : EPSM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+EPSM_API epsm_status epsm_create(epsm_ctx **out, int device, uint64_t flags) {
+    (void)flags;
+    if (!out) return EPSM_ERR_ARG;
+    *out = nullptr;
+    epsm_ctx *c = new (std::nothrow) epsm_ctx();
+    if (!c) return EPSM_ERR_NOMEM;
+    c->errbuf[0] = 0;
+    c->device = device;
+    for (uint32_t m = 0; m <= EPSM_MAX_M; ++m) c->variant[m] = m ? default_variant(m) : 0;
+    auto fail = [&](epsm_status st) {
+        epsm_destroy(c);
+        return st;
+    };
+    cudaError_t e;
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return fail(cuda_fail(nullptr, e, "cudaSetDevice"));
+    if ((e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess)
+        return fail(cuda_fail(nullptr, e, "attr"));
+    if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return fail(cuda_fail(nullptr, e, "stream"));
+    if ((e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming)) != cudaSuccess)
+        return fail(cuda_fail(nullptr, e, "event"));
+    if ((e = cudaMalloc(&c->misc, sizeof(DevMisc))) != cudaSuccess) return fail(cuda_fail(nullptr, e, "misc"));
+    if ((e = cudaMallocHost(&c->hmisc, sizeof(DevMisc))) != cudaSuccess)
+        return fail(cuda_fail(nullptr, e, "hmisc"));
+    if ((e = cudaMemset(c->misc, 0, sizeof(DevMisc))) != cudaSuccess) return fail(cuda_fail(nullptr, e, "memset"));
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(cuda_fail(nullptr, e, "sync"));
+    *out = c;
+    return EPSM_OK;
+}
+
+EPSM_API epsm_status epsm_destroy(epsm_ctx *c) {
+    if (!c) return EPSM_OK;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaDeviceSynchronize();
+    if (c->status) cudaFree(c->status);
+    if (c->misc) cudaFree(c->misc);
+    if (c->hmisc) cudaFreeHost(c->hmisc);
+    if (c->hpairs) cudaFreeHost(c->hpairs);
+    if (c->dpairs) cudaFree(c->dpairs);
+    if (c->hoffsets) cudaFreeHost(c->hoffsets);
+    if (c->doffsets) cudaFree(c->doffsets);
+    if (c->seg_count) cudaFree(c->seg_count);
+    if (c->seg_mask) cudaFree(c->seg_mask);
+    if (c->dtext) cudaFree(c->dtext);
+    if (c->dpos) cudaFree(c->dpos);
+    if (c->ev) cudaEventDestroy(c->ev);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return EPSM_OK;
+}
+
+EPSM_API const char *epsm_status_str(epsm_status s) {
+    switch (s) {
+        case EPSM_OK: return "EPSM_OK";
+        case EPSM_ERR_ARG: return "EPSM_ERR_ARG";
+        case EPSM_ERR_CAPACITY: return "EPSM_ERR_CAPACITY";
+        case EPSM_ERR_CUDA: return "EPSM_ERR_CUDA";
+        case EPSM_ERR_NOMEM: return "EPSM_ERR_NOMEM";
+        case EPSM_ERR_TIMEOUT: return "EPSM_ERR_TIMEOUT";
+        default: return "EPSM_ERR_UNKNOWN";
+    }
+}
+
+EPSM_API const char *epsm_last_error(epsm_ctx *c) { return c ? c->errbuf : ""; }
+
+EPSM_API epsm_status epsm_search_async(epsm_ctx *c, const uint8_t *text, uint64_t n,
+                                       const uint8_t *pattern, uint32_t m, uint64_t *positions,
+                                       uint64_t capacity, uint64_t *count_dev, void *stream) {
+    return search_async_impl(c, EPSM_VARIANT_AUTO, text, n, pattern, m, positions, capacity,
+                             count_dev, stream, 0);
+}
+
+EPSM_API epsm_status epsm_search_variant(epsm_ctx *c, int variant, const uint8_t *text,
+                                         uint64_t n, const uint8_t *pattern, uint32_t m,
+                                         uint64_t *positions, uint64_t capacity,
+                                         uint64_t *count_dev, void *stream) {
+    return search_async_impl(c, variant, text, n, pattern, m, positions, capacity, count_dev,
+                             stream, 0);
+}
+
+EPSM_API epsm_status epsm_search(epsm_ctx *c, const uint8_t *text, uint64_t n,
+                                 const uint8_t *pattern, uint32_t m, uint64_t *positions,
+                                 uint64_t capacity, uint64_t *count, void *stream) {
+    if (!c || !count) return EPSM_ERR_ARG;
+    epsm_status st = search_async_impl(c, EPSM_VARIANT_AUTO, text, n, pattern, m, positions,
+                                       capacity, &c->misc->count, stream, 0);
+    if (st != EPSM_OK) return st;
+    uint32_t err = 0;
+    if ((st = read_misc(c, pick_stream(c, stream), &err)) != EPSM_OK) return st;
+    *count = c->hmisc->count;
+    if (err & kErrTimeout) return EPSM_ERR_TIMEOUT;
+    return *count > capacity ? EPSM_ERR_CAPACITY : EPSM_OK;
+}
+
+EPSM_API epsm_status epsm_sync(epsm_ctx *c, void *stream) {
+    if (!c) return EPSM_ERR_ARG;
+    uint32_t err = 0;
+    epsm_status st = read_misc(c, pick_stream(c, stream), &err);
+    if (st != EPSM_OK) return st;
+    if (err & kErrTimeout) return EPSM_ERR_TIMEOUT;
+    if (err & kErrCapacity) return EPSM_ERR_CAPACITY;
+    return EPSM_OK;
+}
+
+EPSM_API epsm_status epsm_search_batch(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts,
+                                       const uint64_t *ns, const uint8_t *const *patterns,
+                                       const uint32_t *ms, uint64_t *positions, uint64_t capacity,
+                                       uint64_t *offsets, void *stream) {
+    if (!c || !offsets) return EPSM_ERR_ARG;
+    if (npairs == 0) {
+        offsets[0] = 0;
+        return EPSM_OK;
+    }
+    if (!texts || !ns || !patterns || !ms) return EPSM_ERR_ARG;
+    if (capacity > 0 && !positions) return EPSM_ERR_ARG;
+    for (uint32_t i = 0; i < npairs; ++i) {
+        if (ms[i] == 0 || ms[i] > EPSM_MAX_M || !patterns[i]) return EPSM_ERR_ARG;
+        if (ns[i] > 0 && !texts[i]) return EPSM_ERR_ARG;
+    }
+    return batch_impl(c, npairs, texts, ns, patterns, ms, positions, capacity, offsets,
+                      pick_stream(c, stream));
+}
+
+EPSM_API epsm_status epsm_search_host(epsm_ctx *c, const uint8_t *text_host, uint64_t n,
+                                      const uint8_t *patterns_host, const uint32_t *ms,
+                                      uint32_t npat, uint64_t *positions_host, uint64_t capacity,
+                                      uint64_t *offsets_host) {
+    if (!c || !offsets_host || (n > 0 && !text_host)) return EPSM_ERR_ARG;
+    if (npat > 0 && (!patterns_host || !ms)) return EPSM_ERR_ARG;
+    if (capacity > 0 && !positions_host) return EPSM_ERR_ARG;
+    cudaStream_t s = c->stream;
+    if (n + 16 > c->dtext_cap) {
+        CK(cudaStreamSynchronize(s));
+        if (c->dtext) CK(cudaFree(c->dtext));
+        c->dtext = nullptr;
+        c->dtext_cap = 0;
+        CK(cudaMalloc(&c->dtext, n + 16));
+        c->dtext_cap = n + 16;
+    }
+    if (capacity > c->dpos_cap) {
+        CK(cudaStreamSynchronize(s));
+        if (c->dpos) CK(cudaFree(c->dpos));
+        c->dpos = nullptr;
+        c->dpos_cap = 0;
+        CK(cudaMalloc(&c->dpos, capacity * sizeof(uint64_t)));
+        c->dpos_cap = capacity;
+    }
+    epsm_status st = order_after_previous(c, s);
+    if (st != EPSM_OK) return st;
+    if (n) CK(cudaMemcpyAsync(c->dtext, text_host, n, cudaMemcpyHostToDevice, s));
+    std::vector<const uint8_t *> texts(npat, c->dtext), pats(npat);
+    std::vector<uint64_t> ns(npat, n);
+    uint64_t off = 0;
+    for (uint32_t k = 0; k < npat; ++k) {
+        if (ms[k] == 0 || ms[k] > EPSM_MAX_M) return EPSM_ERR_ARG;
+        pats[k] = patterns_host + off;
+        off += ms[k];
+    }
+    if (npat == 0) {
+        offsets_host[0] = 0;
+        return mark_done(c, s);
+    }
+    st = batch_impl(c, npat, texts.data(), ns.data(), pats.data(), ms, c->dpos, capacity,
+                    offsets_host, s);
+    if (st != EPSM_OK && st != EPSM_ERR_CAPACITY) return st;
+    uint64_t got = std::min<uint64_t>(offsets_host[npat], capacity);
+    if (got) {
+        CK(cudaMemcpyAsync(positions_host, c->dpos, got * sizeof(uint64_t),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return st;
+}
+
+EPSM_API int epsm_variant_for(epsm_ctx *c, uint32_t m) {
+    if (!c || m == 0 || m > EPSM_MAX_M) return 0;
+    return c->variant[m];
+}
+
+EPSM_API epsm_status epsm_set_variant(epsm_ctx *c, uint32_t m, int variant) {
+    if (!c || m == 0 || m > EPSM_MAX_M) return EPSM_ERR_ARG;
+    if (!variant_covers(variant, m)) return EPSM_ERR_ARG;
+    c->variant[m] = variant;
+    return EPSM_OK;
+}
+
+EPSM_API uint64_t epsm_launch_count(epsm_ctx *c) { return c ? c->launches : 0; }

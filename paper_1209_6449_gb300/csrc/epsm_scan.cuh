@@ -1,0 +1,345 @@
+// Device building blocks of the exact short-pattern scan (sm_103a).
+//
+// A search is the problem of Section 1: all s in [0, n-m] with t[s..s+m) == p.
+// The text is processed in tiles; each warp streams 16-byte chunks with
+// coalesced vector loads, a per-variant filter marks candidate starts (the
+// Section 3 procedures re-thought for 32-bit lanes), candidates are verified,
+// and the hits of a tile are compacted in order: warp ballot/popc and block
+// prefix sums inside the tile, a decoupled look-back across tiles for the
+// tile's global output offset.
+//
+// Coordinates.  `base` is the text pointer rounded down to 16 bytes and
+// `delta` = text - base.  An internal position P addresses base[P]; the user
+// position is s = P - delta.  Valid starts are delta <= P <= pmax = delta+n-m.
+// Chunk c covers internal bytes [16c, 16c+16).  Only bytes inside
+// [delta, delta+n) are ever read: whole-chunk vector loads are used when the
+// chunk lies inside, byte loads at the two ragged ends.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace epsm {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr uint32_t kFull = 0xffffffffu;
+
+// Variants (see include/epsm.h).
+constexpr int V_DIRECT = 1;
+constexpr int V_PREFIX4 = 2;
+constexpr int V_PREFIX8 = 3;
+constexpr int V_BLOCK8 = 4;
+
+// Block fingerprint table (Section 3.4): k = 11 bits -> 2048 one-byte slots.
+constexpr int kHashBits = 11;
+constexpr int kHashSlots = 1 << kHashBits;
+
+// Error bits of the device error word.
+constexpr uint32_t kErrTimeout = 1u;   // a look-back wait gave up
+constexpr uint32_t kErrCapacity = 2u;  // an occurrence did not fit in the output
+
+// Tile status word: [63:42] call tag, [41:40] flag, [39:0] value.
+constexpr int kTagShift = 42;
+constexpr int kFlagShift = 40;
+constexpr uint64_t kValMask = (1ull << 40) - 1;
+constexpr uint32_t kFlagAgg = 1;
+constexpr uint32_t kFlagPre = 2;
+constexpr uint64_t kLookbackTimeoutNs = 2000000000ull;  // 2 s per wait
+
+// Look-back tuning.  Status words are spread kStatusStride words apart so that
+// the words of recent tiles, which every block polls, fall on different L2
+// lines instead of all on a few (a hot spot that serialised the polls).
+#ifndef EPSM_LB_K
+#define EPSM_LB_K 1
+#endif
+#ifndef EPSM_LB_STRIDE
+#define EPSM_LB_STRIDE 16
+#endif
+#ifndef EPSM_LB_HELP
+#define EPSM_LB_HELP 0
+#endif
+#ifndef EPSM_LB_SLEEP
+#define EPSM_LB_SLEEP 128
+#endif
+constexpr int kLookbackK = EPSM_LB_K;          // status words per lane per round
+constexpr int kStatusStride = EPSM_LB_STRIDE;  // uint64 words between tiles' status
+constexpr bool kLookbackHelp = EPSM_LB_HELP != 0;
+constexpr int kLookbackSleepNs = EPSM_LB_SLEEP;
+
+struct Pattern {
+    uint32_t w[8];  // p packed little-endian, zero padded (the paper's blocks P_i, Section 2)
+    uint32_t m;
+};
+
+struct SearchJob {
+    const uint8_t *base;  // text rounded down to 16 bytes
+    uint64_t delta;       // text - base
+    uint64_t lim;         // delta + n: first internal byte past the text
+    int64_t pmax;         // delta + n - m: last valid internal start
+    Pattern pat;
+};
+
+// ---------------------------------------------------------------------------
+// memory helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint4 ldg_v4(const uint8_t *p) {
+    uint4 r;
+    asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t ldg_u32(const uint8_t *p) {
+    uint32_t r;
+    asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(r) : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t ldg_u8(const uint8_t *p) {
+    uint16_t r;
+    asm volatile("ld.global.nc.u8 %0, [%1];" : "=h"(r) : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// The 16-byte chunk c of the text; bytes outside [delta, lim) read as 0.
+__device__ __forceinline__ uint4 load_chunk(const SearchJob &J, uint64_t c) {
+    uint64_t b0 = c * 16ull;
+    if (b0 >= J.delta && b0 + 16ull <= J.lim) return ldg_v4(J.base + b0);
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    if (b0 + 16ull > J.delta && b0 < J.lim) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            uint64_t b = b0 + (uint64_t)i;
+            if (b >= J.delta && b < J.lim) w[i >> 2] |= ldg_u8(J.base + b) << (8 * (i & 3));
+        }
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// 4-byte word widx of the text; bytes outside [delta, lim) read as 0.
+__device__ __forceinline__ uint32_t load_word(const SearchJob &J, uint64_t widx) {
+    uint64_t b0 = widx * 4ull;
+    if (b0 >= J.delta && b0 + 4ull <= J.lim) return ldg_u32(J.base + b0);
+    uint32_t w = 0u;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        uint64_t b = b0 + (uint64_t)i;
+        if (b >= J.delta && b < J.lim) w |= ldg_u8(J.base + b) << (8 * i);
+    }
+    return w;
+}
+
+// ---------------------------------------------------------------------------
+// packed-byte helpers (the wscmp idea of Section 3.1 on 32-bit lanes)
+// ---------------------------------------------------------------------------
+
+// Exact zero-byte mask: bit 8b+7 set iff byte b of x is zero.
+__device__ __forceinline__ uint32_t zero_bytes(uint32_t x) {
+    uint32_t y = (x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu;
+    return ~(y | x | 0x7F7F7F7Fu);
+}
+
+// Nonzero iff some byte of x is zero (exact as a test, not as a mask).
+__device__ __forceinline__ uint32_t has_zero_byte(uint32_t x) {
+    return (x - 0x01010101u) & ~x & 0x80808080u;
+}
+
+// Bits 7,15,23,31 of z -> bits 0..3.
+__device__ __forceinline__ uint32_t nibble_of(uint32_t z) {
+    return ((z >> 7) * 0x10204080u) >> 28;
+}
+
+// Byte j of w replicated four times: the broadcast word (p_j)^4 (Section 3.2, table B).
+__device__ __forceinline__ uint32_t bcast_byte(uint32_t w, int j) {
+    return __byte_perm(w, 0u, (uint32_t)(j * 0x1111));
+}
+
+// Multiplicative (Fibonacci) hash of an 8-byte block to kHashBits bits.
+__device__ __forceinline__ uint32_t block_hash(uint32_t lo, uint32_t hi) {
+    return (lo * 0x9E3779B1u + hi * 0x85EBCA77u) >> (32 - kHashBits);
+}
+
+// Mask of the bytes of pattern word i that belong to the pattern.
+__device__ __forceinline__ uint32_t word_mask(uint32_t m, uint32_t i) {
+    uint32_t rem = m - 4u * i;
+    return rem >= 4u ? 0xFFFFFFFFu : ((1u << (8u * rem)) - 1u);
+}
+
+// Naive check (Section 3, "check position"): t[P..P+m) == p, read from global.
+__device__ __noinline__ bool verify_global(const SearchJob &J, int64_t P) {
+    uint64_t a = (uint64_t)P >> 2;
+    uint32_t sh = ((uint32_t)P & 3u) * 8u;
+    uint32_t m = J.pat.m;
+    uint32_t nw = (m + 3u) >> 2;
+    uint32_t cur = load_word(J, a);
+    for (uint32_t i = 0; i < nw; ++i) {
+        uint32_t nxt = (sh != 0u || i + 1u < nw) ? load_word(J, a + i + 1u) : 0u;
+        uint32_t win = __funnelshift_r(cur, nxt, sh);
+        if ((win ^ J.pat.w[i]) & word_mask(m, i)) return false;
+        cur = nxt;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// warp scans
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t t = __shfl_up_sync(kFull, v, d);
+        if (lane >= d) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+    return v;
+}
+
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// decoupled look-back across tiles (called by one full warp)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t pack_status(uint32_t tag, uint32_t flag, uint64_t v) {
+    return ((uint64_t)tag << kTagShift) | ((uint64_t)flag << kFlagShift) | (v & kValMask);
+}
+
+// Publishes the tile aggregate, walks back over its predecessors 32*K at a
+// time (K consecutive status words per lane) until one holds an inclusive
+// prefix, publishes this tile's inclusive prefix, and returns the exclusive
+// prefix (in every lane).  An inclusive prefix thus travels 32*K tiles per
+// round trip to L2; with 32 tiles per round trip the prefix chain, not HBM,
+// bounded the scan.  Each wait is bounded in time; on expiry the error word
+// gets kErrTimeout and the wait is abandoned (missing values count as 0), so
+// the kernel always terminates.
+template <int K = kLookbackK>
+__device__ uint64_t tile_lookback(uint64_t *status, uint64_t tile, uint64_t agg, uint32_t tag,
+                                  uint32_t *err, int lane) {
+    if (tile == 0) {
+        if (lane == 0) st_relaxed_u64(status, pack_status(tag, kFlagPre, agg));
+        return 0;
+    }
+    if (lane == 0) st_relaxed_u64(status + tile * kStatusStride, pack_status(tag, kFlagAgg, agg));
+    uint64_t excl = 0;
+    int64_t end = (int64_t)tile;  // window: tiles end-1 down to end-32K
+    uint64_t t0 = 0;
+    bool timed_out = false;
+    while (true) {
+        uint64_t v[K];
+        uint32_t f[K];
+        int fl, lp;
+        while (true) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const int64_t idx = end - 1 - (int64_t)(lane * K + j);
+                if (idx >= 0) {
+                    const uint64_t s = ld_relaxed_u64(status + idx * kStatusStride);
+                    f[j] = ((uint32_t)(s >> kTagShift) == tag) ? (uint32_t)(s >> kFlagShift) & 3u : 0u;
+                    v[j] = s & kValMask;
+                } else {
+                    f[j] = kFlagPre;  // before tile 0: an empty prefix
+                    v[j] = 0;
+                }
+            }
+            lp = K;
+#pragma unroll
+            for (int j = K - 1; j >= 0; --j)
+                if (f[j] == kFlagPre) lp = j;
+            const uint32_t pb = __ballot_sync(kFull, lp < K);
+            fl = pb ? __ffs(pb) - 1 : 32;
+            // tiles up to the nearest inclusive prefix must have published
+            bool ready = true;
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (lane < fl || (lane == fl && j <= lp)) ready &= f[j] != 0u;
+            if (__all_sync(kFull, ready)) break;
+            if (timed_out) {
+#pragma unroll
+                for (int j = 0; j < K; ++j)
+                    if (f[j] == 0u) { f[j] = kFlagPre; v[j] = 0; }
+                lp = K;
+#pragma unroll
+                for (int j = K - 1; j >= 0; --j)
+                    if (f[j] == kFlagPre) lp = j;
+                const uint32_t pb2 = __ballot_sync(kFull, lp < K);
+                fl = pb2 ? __ffs(pb2) - 1 : 32;
+                break;
+            }
+            const uint64_t now = globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            if (__any_sync(kFull, now - t0 > kLookbackTimeoutNs)) {
+                timed_out = true;
+                if (lane == 0) atomicOr(err, kErrTimeout);
+            }
+            __nanosleep(kLookbackSleepNs);
+        }
+        uint64_t mine = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (lane < fl || (lane == fl && j <= lp)) mine += v[j];
+        const uint64_t wsum = warp_sum64(mine);
+        if (kLookbackHelp && fl < 32 && end == (int64_t)tile && !timed_out) {
+            // Help the prefix chain: every predecessor between the inclusive
+            // prefix found and this tile gets its own inclusive prefix,
+            // excl_total - (sum of the aggregates after it), so later tiles
+            // find one close by instead of waiting for each owner in turn.
+            const uint64_t total = excl + wsum;  // exclusive prefix of `tile`
+            uint64_t lane_sum = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (lane < fl || (lane == fl && j <= lp)) lane_sum += v[j];
+            uint64_t before = lane_sum;  // inclusive scan over lanes of lane_sum
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint64_t t = __shfl_up_sync(kFull, before, d);
+                if (lane >= d) before += t;
+            }
+            before -= lane_sum;  // sum of the aggregates of tiles closer to `tile`
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const bool in = lane < fl || (lane == fl && j < lp);
+                if (in && f[j] == kFlagAgg) {
+                    const int64_t idx = end - 1 - (int64_t)(lane * K + j);
+                    st_relaxed_u64(status + idx * kStatusStride,
+                                   pack_status(tag, kFlagPre, total - before));
+                }
+                if (lane < fl || (lane == fl && j <= lp)) before += v[j];
+            }
+        }
+        excl += wsum;
+        if (fl < 32) break;
+        end -= 32 * K;
+    }
+    if (lane == 0) st_relaxed_u64(status + tile * kStatusStride, pack_status(tag, kFlagPre, excl + agg));
+    return excl;
+}
+
+}  // namespace epsm

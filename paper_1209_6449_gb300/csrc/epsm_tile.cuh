@@ -1,0 +1,317 @@
+// Per-tile scan: filter, verify, in-tile compaction, look-back, ordered emit.
+//
+// Tile layout.  A tile is kThreads*U consecutive 16-byte chunks.  Warp w owns
+// the 32*U chunks starting at tile_chunk0 + 32*U*w; at step u lane l holds chunk
+// 32*u + l of that run (every load instruction of the warp covers 512
+// contiguous bytes).  The bytes a window needs beyond its own chunk come from
+// the next lane's registers (one shuffle per word); lane 31 takes them from
+// lane 0's chunk of step u+1, and at the last step from a halo chunk that lane
+// 0 loads after the warp's run.
+//
+// Hit masks.  For each chunk a 16-bit mask marks hits: bit i <-> internal
+// start pos0 + OFF + i, with pos0 = 16*chunk.  OFF = 0 for the window variants;
+// the block variant reports candidate s = 8b - j from block b, j in [0, 8), so
+// a chunk's two blocks cover starts [pos0 - 7, pos0 + 8] and OFF = -7.  Masks
+// are in ascending position order across (warp, step, lane, bit), which is
+// the order positions are written in.
+#pragma once
+
+#include "epsm_scan.cuh"
+
+namespace epsm {
+
+struct TileSmem {
+    uint32_t next_tile;
+    uint32_t tile_total;
+    uint64_t tile_off;
+    uint32_t warp_off[kWarps];
+    uint32_t pblk[16];              // block variant: p[j..j+7] as (lo, hi), j = 0..7
+    uint8_t table[kHashSlots];      // block variant: fingerprint slots (Section 3.4, table L)
+};
+
+struct TileOut {
+    uint64_t *positions;  // device, ascending output (global index space)
+    uint64_t capacity;    // entries available in positions
+    uint64_t *status;     // look-back status words, indexed by global tile
+    uint32_t *err;        // device error word
+    uint32_t tag;         // call tag for status words
+};
+
+// Pattern preprocessing for the block variant (Section 3.4, table L): the
+// fingerprints of the eight pattern blocks p[j..j+7], j = 0..7.  Must be
+// called by all threads of the block; ends with a barrier.
+__device__ __forceinline__ void build_block_table(const Pattern &pat, uint8_t *table,
+                                                  uint32_t *pblk) {
+    uint32_t *tw = reinterpret_cast<uint32_t *>(table);
+    for (int i = threadIdx.x; i < kHashSlots / 4; i += blockDim.x) tw[i] = 0u;
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        int j = threadIdx.x;
+        int q = j >> 2;
+        uint32_t sh = 8u * (uint32_t)(j & 3);
+        uint32_t lo = __funnelshift_r(pat.w[q], pat.w[q + 1], sh);
+        uint32_t hi = __funnelshift_r(pat.w[q + 1], pat.w[q + 2], sh);
+        pblk[2 * j] = lo;
+        pblk[2 * j + 1] = hi;
+        table[block_hash(lo, hi)] = 1;
+    }
+    __syncthreads();
+}
+
+// Broadcast words (p_j)^4 of the first eight pattern bytes (Section 3.2, table B).
+struct BcastWords {
+    uint32_t b[8];
+    __device__ __forceinline__ explicit BcastWords(const Pattern &pat) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) b[j] = bcast_byte(pat.w[j >> 2], j & 3);
+    }
+};
+
+// Mismatch word of a 4-byte pattern piece at the 4 starts of word R0 (R1 next):
+// byte k is zero iff t[4w+k .. 4w+k+3] equals the piece (b0..b3 broadcast).
+template <int NB>
+__device__ __forceinline__ uint32_t window_mismatch(uint32_t acc, uint32_t R0, uint32_t R1,
+                                                    uint32_t b0, uint32_t b1, uint32_t b2,
+                                                    uint32_t b3) {
+    acc |= R0 ^ b0;
+    if (NB > 1) acc |= __funnelshift_r(R0, R1, 8) ^ b1;
+    if (NB > 2) acc |= __funnelshift_r(R0, R1, 16) ^ b2;
+    if (NB > 3) acc |= __funnelshift_r(R0, R1, 24) ^ b3;
+    return acc;
+}
+
+// 16-bit mask of bits [lo, hi] (clipped to 0..15); 0 if empty.
+__device__ __forceinline__ uint32_t range_mask(int64_t lo, int64_t hi) {
+    if (hi < 0 || lo > 15 || lo > hi) return 0u;
+    int a = lo < 0 ? 0 : (int)lo;
+    int b = hi > 15 ? 15 : (int)hi;
+    return (0xFFFFu >> (15 - b)) & (0xFFFFu << a) & 0xFFFFu;
+}
+
+// In-register verify of pattern words [w_from, nw) for the start at byte b of
+// word K of the chunk; RR holds the chunk's words and the next chunk's words.
+template <int K>
+__device__ __forceinline__ bool verify_regs(const uint32_t (&RR)[8], uint32_t b, uint32_t w_from,
+                                            const Pattern &pat) {
+    uint32_t m = pat.m;
+    uint32_t nw = (m + 3u) >> 2;
+    bool ok = true;
+#pragma unroll
+    for (int i = 1; i < 4; ++i) {
+        if ((uint32_t)i >= w_from && (uint32_t)i < nw) {
+            uint32_t win = __funnelshift_r(RR[K + i], RR[K + i + 1], 8u * b);
+            ok &= ((win ^ pat.w[i]) & word_mask(m, (uint32_t)i)) == 0u;
+        }
+    }
+    return ok;
+}
+
+template <int K>
+__device__ __forceinline__ uint32_t verify_word_hits(uint32_t z, const uint32_t (&RR)[8],
+                                                     uint32_t w_from, const Pattern &pat) {
+    uint32_t h = 0u;
+    while (z) {
+        uint32_t b = (uint32_t)(__ffs(z) >> 3) - 1u;
+        z &= z - 1u;
+        if (verify_regs<K>(RR, b, w_from, pat)) h |= 1u << (4 * K + b);
+    }
+    return h;
+}
+
+// Block variant, slow path: one of the chunk's two blocks hit a marked
+// fingerprint slot.  Compare the blocks with the pattern blocks p[j..j+7]; a
+// block match at j gives the candidate 8b - j, which is checked in full.
+__device__ __noinline__ uint32_t block_candidates(const SearchJob &J, const uint4 cur, int64_t p0,
+                                                  const uint32_t *pblk, uint32_t t0, uint32_t t1) {
+    uint32_t cand = 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t lo = pblk[2 * j], hi = pblk[2 * j + 1];
+        if (t0 && cur.x == lo && cur.y == hi) cand |= 1u << (7 - j);
+        if (t1 && cur.z == lo && cur.w == hi) cand |= 1u << (15 - j);
+    }
+    uint32_t h = 0u;
+    while (cand) {
+        int i = __ffs(cand) - 1;
+        cand &= cand - 1u;
+        int64_t P = p0 + i;
+        if (P >= (int64_t)J.delta && P <= J.pmax && verify_global(J, P)) h |= 1u << i;
+    }
+    return h;
+}
+
+// Hit mask of one chunk (before start-validity masking).
+//   cur    the chunk's words; nsrc: this lane's contribution to the neighbour
+//   shuffle (the chunk the lane before needs as "next chunk").
+template <int V, int MP>
+__device__ __forceinline__ uint32_t chunk_hits(const SearchJob &J, const uint4 cur,
+                                               const uint4 nsrc, int64_t p0,
+                                               const BcastWords &B, const uint8_t *table,
+                                               const uint32_t *pblk, int lane) {
+    const int src = (lane + 1) & 31;
+    const Pattern &pat = J.pat;
+    if constexpr (V == V_DIRECT) {
+        // Section 3.2 (EPSMa): every start is compared against the whole
+        // (m <= 4) pattern at once; no verify step.
+        uint32_t n0 = __shfl_sync(kFull, nsrc.x, src);
+        uint32_t R[5] = {cur.x, cur.y, cur.z, cur.w, n0};
+        uint32_t h = 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t X = window_mismatch<MP>(0u, R[k], R[k + 1], B.b[0], B.b[1], B.b[2], B.b[3]);
+            h |= nibble_of(zero_bytes(X)) << (4 * k);
+        }
+        return h;
+    } else if constexpr (V == V_PREFIX4) {
+        // Section 3.3 (EPSMb) with a 4-byte prefix: exact prefix test per start,
+        // then the remaining bytes are checked in registers.
+        uint32_t n0 = __shfl_sync(kFull, nsrc.x, src);
+        uint32_t R[5] = {cur.x, cur.y, cur.z, cur.w, n0};
+        uint32_t X[4];
+        uint32_t any = 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            X[k] = window_mismatch<4>(0u, R[k], R[k + 1], B.b[0], B.b[1], B.b[2], B.b[3]);
+            any |= has_zero_byte(X[k]);
+        }
+        uint32_t h = 0u;
+        if (__any_sync(kFull, any != 0u)) {
+            uint32_t n1 = __shfl_sync(kFull, nsrc.y, src);
+            uint32_t n2 = __shfl_sync(kFull, nsrc.z, src);
+            uint32_t n3 = __shfl_sync(kFull, nsrc.w, src);
+            const uint32_t RR[8] = {cur.x, cur.y, cur.z, cur.w, n0, n1, n2, n3};
+            if (any) {
+                h |= verify_word_hits<0>(zero_bytes(X[0]), RR, 1u, pat);
+                h |= verify_word_hits<1>(zero_bytes(X[1]), RR, 1u, pat);
+                h |= verify_word_hits<2>(zero_bytes(X[2]), RR, 1u, pat);
+                h |= verify_word_hits<3>(zero_bytes(X[3]), RR, 1u, pat);
+            }
+        }
+        return h;
+    } else if constexpr (V == V_PREFIX8) {
+        // Section 3.3 (EPSMb) with the paper's m' = 8 prefix: the prefix
+        // mismatch at start 4k+b is byte b of X_k | Y_{k+1}, X for p[0..3] at
+        // word k and Y for p[4..7] at word k+1.
+        uint32_t n0 = __shfl_sync(kFull, nsrc.x, src);
+        uint32_t n1 = __shfl_sync(kFull, nsrc.y, src);
+        uint32_t R[6] = {cur.x, cur.y, cur.z, cur.w, n0, n1};
+        uint32_t Z[4];
+        uint32_t any = 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t X = window_mismatch<4>(0u, R[k], R[k + 1], B.b[0], B.b[1], B.b[2], B.b[3]);
+            Z[k] = window_mismatch<4>(X, R[k + 1], R[k + 2], B.b[4], B.b[5], B.b[6], B.b[7]);
+            any |= has_zero_byte(Z[k]);
+        }
+        uint32_t h = 0u;
+        if (__any_sync(kFull, any != 0u)) {
+            uint32_t n2 = __shfl_sync(kFull, nsrc.z, src);
+            uint32_t n3 = __shfl_sync(kFull, nsrc.w, src);
+            const uint32_t RR[8] = {cur.x, cur.y, cur.z, cur.w, n0, n1, n2, n3};
+            if (any) {
+                h |= verify_word_hits<0>(zero_bytes(Z[0]), RR, 2u, pat);
+                h |= verify_word_hits<1>(zero_bytes(Z[1]), RR, 2u, pat);
+                h |= verify_word_hits<2>(zero_bytes(Z[2]), RR, 2u, pat);
+                h |= verify_word_hits<3>(zero_bytes(Z[3]), RR, 2u, pat);
+            }
+        }
+        return h;
+    } else {
+        // Section 3.4 (EPSMc) on aligned 8-byte blocks: fingerprint each block,
+        // and where the slot is marked compare the block with the pattern
+        // blocks p[j..j+7]; a block match at j gives the candidate 8b - j,
+        // which is then checked in full.
+        const uint32_t h0 = block_hash(cur.x, cur.y);
+        const uint32_t h1 = block_hash(cur.z, cur.w);
+        const uint32_t t0 = table[h0];
+        const uint32_t t1 = table[h1];
+        if (t0 | t1) return block_candidates(J, cur, p0, pblk, t0, t1);
+        return 0u;
+    }
+}
+
+// Scan one tile of job J.  `gtile` indexes the look-back status words,
+// `ltile` is the tile's index inside the job.  Returns nothing; writes the
+// tile's positions at out_base + (exclusive prefix of gtile).
+//   count_out: if non-null, receives exclusive+total (the job total when this
+//   is the job's last tile); first_out: if non-null, receives the exclusive
+//   prefix (the job's output offset when this is the job's first tile).
+template <int V, int U, int MP>
+__device__ __forceinline__ void scan_tile(const SearchJob &J, uint64_t ltile, uint64_t gtile,
+                                          const BcastWords &B, TileSmem &sm, const TileOut &O,
+                                          uint64_t *count_out, uint64_t *first_out,
+                                          int64_t pos_bias) {
+    constexpr int OFF = (V == V_BLOCK8) ? -7 : 0;
+    constexpr uint64_t kTileChunks = (uint64_t)kThreads * U;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const uint64_t c0 = ltile * kTileChunks + (uint64_t)warp * 32u * U;
+
+    uint4 ch[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) ch[u] = load_chunk(J, c0 + 32u * u + lane);
+    uint4 halo = make_uint4(0u, 0u, 0u, 0u);
+    if (V != V_BLOCK8 && lane == 0) halo = load_chunk(J, c0 + 32u * U);
+
+    const int64_t tp0 = (int64_t)(ltile * kTileChunks * 16u) + OFF;
+    const bool interior = tp0 >= (int64_t)J.delta &&
+                          tp0 + (int64_t)(kTileChunks * 16u) - 1 <= J.pmax;
+
+    uint32_t hit[U];
+    uint32_t cnt = 0u;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const uint4 cur = ch[u];
+        const uint4 nsrc = (lane == 0) ? (u + 1 < U ? ch[u + 1 < U ? u + 1 : u] : halo) : cur;
+        const int64_t p0 = (int64_t)((c0 + 32u * u + lane) * 16u) + OFF;
+        uint32_t h = chunk_hits<V, MP>(J, cur, nsrc, p0, B, sm.table, sm.pblk, lane);
+        if (!interior) h &= range_mask((int64_t)J.delta - p0, J.pmax - p0);
+        hit[u] = h;
+        cnt += __popc(h);
+    }
+
+    // in-tile prefix sums: warp totals -> block scan (warp 0) -> look-back
+    const uint32_t wt = warp_sum(cnt);
+    if (lane == 0) sm.warp_off[warp] = wt;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t v = lane < kWarps ? sm.warp_off[lane] : 0u;
+        const uint32_t inc = warp_incl_scan(v, lane);
+        const uint32_t total = __shfl_sync(kFull, inc, 31);
+        if (lane < kWarps) sm.warp_off[lane] = inc - v;
+        const uint64_t excl = tile_lookback(O.status, gtile, total, O.tag, O.err, lane);
+        if (lane == 0) {
+            sm.tile_off = excl;
+            sm.tile_total = total;
+            if (count_out) *count_out = excl + total;
+            if (first_out) *first_out = excl;
+        }
+    }
+    __syncthreads();
+
+    if (sm.tile_total != 0u && O.capacity != 0ull) {
+        uint64_t base = sm.tile_off + sm.warp_off[warp];
+        uint32_t run = 0u;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint32_t c = __popc(hit[u]);
+            if (__any_sync(kFull, c != 0u)) {
+                const uint32_t inc = warp_incl_scan(c, lane);
+                uint64_t idx = base + run + inc - c;
+                const int64_t s0 = (int64_t)((c0 + 32u * u + lane) * 16u) + OFF -
+                                   (int64_t)J.delta + pos_bias;
+                uint32_t hh = hit[u];
+                if (hh && idx + __popc(hh) > O.capacity) atomicOr(O.err, kErrCapacity);
+                while (hh) {
+                    const int i = __ffs(hh) - 1;
+                    hh &= hh - 1u;
+                    if (idx < O.capacity) O.positions[idx] = (uint64_t)(s0 + i);
+                    ++idx;
+                }
+                run += __shfl_sync(kFull, inc, 31);
+            }
+        }
+    }
+}
+
+}  // namespace epsm

@@ -1,0 +1,79 @@
+"""C-ABI checks that need no GPU: the library builds, loads, and exports every
+entry point include/epsm.h declares; host-only paths validate arguments; the
+product package never touches the oracle."""
+import ctypes
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "epsm.h")
+
+
+def _built_lib():
+    import __graft_entry__ as g
+    b = g._load_pkg_build()
+    return b.build()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(epsm_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("epsm_create", "epsm_search", "epsm_search_batch", "epsm_destroy",
+                     "epsm_status_str"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib_path = _built_lib()
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(lib_path)
+    for n in declared_functions():
+        assert hasattr(lib, n)
+
+
+def test_status_strings_and_null_context():
+    _built_lib()
+    import paper_1209_6449_gb300 as epsm
+    assert epsm.epsm_status_str(0) == "EPSM_OK"
+    assert epsm.epsm_status_str(5) == "EPSM_ERR_TIMEOUT"
+    lib = epsm._lib
+    cnt = ctypes.c_uint64(7)
+    # NULL context / bad m are rejected on the host before any CUDA call
+    assert lib.epsm_search(None, None, 0, b"a", 1, None, 0, ctypes.byref(cnt), None) == 1
+    assert lib.epsm_search_async(None, None, 0, b"a", 1, None, 0, None, None) == 1
+    assert lib.epsm_destroy(None) == 0
+    assert lib.epsm_variant_for(None, 4) == 0
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    _built_lib()
+    from paper_1209_6449_gb300 import _native
+    with pytest.raises(ImportError):
+        _native.load(str(tmp_path / "nope.so"))
+
+
+def test_package_does_not_reach_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1209_6449_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "liboracle" not in txt and "epsm_oracle" not in txt, f
+    code = ("import sys; sys.path.insert(0, %r); import paper_1209_6449_gb300; "
+            "assert 'oracle' not in sys.modules; print('clean')" % ROOT)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    assert out.returncode == 0 and "clean" in out.stdout, out.stderr

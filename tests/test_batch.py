@@ -1,0 +1,108 @@
+"""GPU parity of the batched persistent launch and of the host-buffer entry
+point: every pair's positions equal the oracle's for that pair alone."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+@pytest.fixture(scope="module")
+def epsm():
+    import paper_1209_6449_gb300 as epsm
+    return epsm
+
+
+@pytest.fixture(scope="module")
+def ctx(epsm):
+    c = epsm.Context(0)
+    yield c
+    c.close()
+
+
+def _pairs(npairs, seed, hi_log2=17):
+    pairs = gen.batch_pairs(npairs, seed=seed, n_lo_log2=0, n_hi_log2=hi_log2)
+    hosts = [p.spec.host(p.n) for p in pairs]
+    return pairs, hosts
+
+
+def _run_batch(ctx, torch, hosts, patterns, offsets_in=None, capacity=None):
+    devs = [torch.from_numpy(h).cuda() if h.size else torch.empty(0, dtype=torch.uint8,
+                                                                   device="cuda") for h in hosts]
+    # unaligned text starts: slice from a 1..15 byte offset into a padded buffer
+    texts = []
+    keep = []
+    for i, h in enumerate(hosts):
+        off = offsets_in[i] if offsets_in else (i * 7) % 16
+        buf = torch.zeros(h.size + off, dtype=torch.uint8, device="cuda")
+        if h.size:
+            buf[off:] = devs[i]
+        keep.append(buf)
+        texts.append((buf.data_ptr() + off, int(h.size)))
+    want = [oracle.search(h, p) for h, p in zip(hosts, patterns)]
+    total = sum(w.size for w in want)
+    cap = total + 8 if capacity is None else capacity
+    offs, out = ctx.search_batch(texts, patterns, cap)
+    torch.cuda.synchronize()
+    return offs, out.cpu().numpy().astype(np.uint64), want, keep
+
+
+def test_batch_matches_oracle_per_pair(ctx, torch):
+    pairs, hosts = _pairs(300, seed=1)
+    pats = [p.pattern for p in pairs]
+    offs, out, want, _ = _run_batch(ctx, torch, hosts, pats)
+    assert offs[-1] == sum(w.size for w in want)
+    for i, w in enumerate(want):
+        got = out[offs[i]:offs[i + 1]]
+        assert np.array_equal(got, w), (i, pairs[i].n, len(pats[i]))
+
+
+def test_batch_order_does_not_change_results(ctx, torch):
+    pairs, hosts = _pairs(120, seed=2)
+    pats = [p.pattern for p in pairs]
+    offs, out, want, _ = _run_batch(ctx, torch, hosts, pats)
+    perm = np.random.default_rng(5).permutation(len(pairs))
+    offs2, out2, _, _ = _run_batch(ctx, torch, [hosts[i] for i in perm], [pats[i] for i in perm],
+                                   offsets_in=[(int(i) * 7) % 16 for i in perm])
+    for k, i in enumerate(perm):
+        assert np.array_equal(out2[offs2[k]:offs2[k + 1]], out[offs[i]:offs[i + 1]])
+
+
+def test_batch_dense_and_degenerate_pairs(ctx, torch):
+    hosts = [np.full(n, ord("a"), dtype=np.uint8) for n in (0, 1, 5, 31, 32, 33, 40000, 70000)]
+    pats = [b"a", b"a" * 2, b"a" * 6, b"a" * 32, b"a" * 32, b"a" * 15, b"a" * 16, b"a" * 3]
+    offs, out, want, _ = _run_batch(ctx, torch, hosts, pats)
+    for i, w in enumerate(want):
+        assert np.array_equal(out[offs[i]:offs[i + 1]], w), i
+
+
+def test_batch_capacity_overflow(ctx, torch, epsm):
+    hosts = [np.full(10000, ord("a"), dtype=np.uint8) for _ in range(3)]
+    pats = [b"aa", b"aaa", b"aaaa"]
+    offs, out, want, _ = _run_batch(ctx, torch, hosts, pats, capacity=15000)
+    assert list(offs) == [0, 9999, 9999 + 9998, 9999 + 9998 + 9997]
+    assert np.array_equal(out[:9999], np.arange(9999))
+    assert np.array_equal(out[9999:15000], np.arange(15000 - 9999))
+
+
+def test_search_host_matches_oracle(ctx):
+    spec = gen.TextSpec("protein", 8)
+    n = 200_000 + 13
+    host = spec.host(n)
+    pats = []
+    for m in (1, 2, 3, 4, 7, 8, 13, 15, 16, 23, 32):
+        pats += gen.mixed_patterns(spec, n, m, 2, stream_seed=m)
+    want = [oracle.search(host, p) for p in pats]
+    total = sum(w.size for w in want)
+    offs, pos = ctx.search_host(host, pats, total + 4)
+    assert offs[-1] == total
+    for k, w in enumerate(want):
+        assert np.array_equal(pos[offs[k]:offs[k + 1]], w), k
