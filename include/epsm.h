@@ -149,6 +149,35 @@ epsm_status epsm_set_variant(epsm_ctx *ctx, uint32_t m, int variant);
 /* Number of kernel launches the context has issued (all entry points). */
 uint64_t epsm_launch_count(epsm_ctx *ctx);
 
+/* Largest text epsm_search_static accepts (bytes). */
+#define EPSM_STATIC_MAX_TEXT (64ull << 20)
+
+/* Single search that allocates nothing and needs no context.
+ *
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not allocate device memory themselves (a framework that routes every
+ * allocation through its own pool, a real-time loop where an allocation could
+ * stall or fail, a plug-in whose host pre-sizes all memory).  The search is the
+ * same as epsm_search_async with the automatic variant; its scratch lives in a
+ * fixed device array of about 8.5 MiB inside the library, which every GPU that
+ * loads the library keeps until the process exits.
+ *   text        device, n bytes, n <= EPSM_STATIC_MAX_TEXT (larger n returns
+ *               EPSM_ERR_ARG without touching the GPU)
+ *   pattern     host, m bytes (1..32)
+ *   positions   device, room for `capacity` uint64 (NULL iff capacity == 0)
+ *   result_dev  device, two uint64: [0] receives the count, [1] the device
+ *               error bits (1: a bounded wait gave up, 2: more occurrences than
+ *               capacity); both are cleared when the call is enqueued
+ * Asynchronous on `stream` (NULL = default stream) on the current device.
+ * The first call on a device looks up the array's device address and the SM
+ * count; make that first call before any stream capture.  Calls share the one
+ * array: calls whose work overlaps on the GPU (different streams, or another
+ * host thread) race and give wrong results; order them on one stream.  It
+ * calls no cudaMalloc, cudaFree or other allocating routine. */
+epsm_status epsm_search_static(const uint8_t *text, uint64_t n, const uint8_t *pattern,
+                               uint32_t m, uint64_t *positions, uint64_t capacity,
+                               uint64_t *result_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,13 +15,13 @@ from typing import Sequence
 import numpy as np
 
 from . import _native
-from ._native import (MAX_M, STATUS_NAMES, VARIANT_AUTO, VARIANT_BLOCK8, VARIANT_DIRECT,
+from ._native import (MAX_M, STATIC_MAX_TEXT, STATUS_NAMES, VARIANT_AUTO, VARIANT_BLOCK8, VARIANT_DIRECT,
                       VARIANT_NAMES, VARIANT_PREFIX4, VARIANT_PREFIX8)
 
 __all__ = ["Context", "EpsmError", "epsm_create", "epsm_destroy", "epsm_status_str",
            "epsm_search", "epsm_search_async", "epsm_search_variant", "epsm_sync",
            "epsm_search_batch", "epsm_search_host", "epsm_variant_for", "epsm_set_variant",
-           "epsm_launch_count", "MAX_M", "VARIANT_AUTO", "VARIANT_DIRECT", "VARIANT_PREFIX4",
+           "epsm_launch_count", "epsm_search_static", "STATIC_MAX_TEXT", "MAX_M", "VARIANT_AUTO", "VARIANT_DIRECT", "VARIANT_PREFIX4",
            "VARIANT_PREFIX8", "VARIANT_BLOCK8", "VARIANT_NAMES"]
 
 _lib = _native.load()
@@ -124,6 +124,14 @@ def epsm_set_variant(ctx: int, m: int, variant: int) -> int:
 
 def epsm_launch_count(ctx: int) -> int:
     return _lib.epsm_launch_count(ctx)
+
+
+def epsm_search_static(text: int, n: int, pattern: bytes, m: int, positions: int,
+                       capacity: int, result_dev: int, stream: int = 0) -> int:
+    """Search with no allocation: scratch is the library's fixed device array.
+    ``result_dev`` points to two device uint64 (count, device error bits)."""
+    return _lib.epsm_search_static(text, n, _buf(pattern), m, positions, capacity, result_dev,
+                                   stream)
 
 
 # ---------------------------------------------------------------------------

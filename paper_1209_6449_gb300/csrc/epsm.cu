@@ -208,7 +208,7 @@ epsm_status next_tag(epsm_ctx *c, cudaStream_t s, uint32_t *tag) {
 // Single searches run the cooperative streaming kernel (epsm_stream.cuh): one
 // block per SM, all co-resident.
 template <int V, int MP>
-cudaError_t launch_stream_t(epsm_ctx *c, const stream::StreamParams &p, cudaStream_t s) {
+cudaError_t launch_stream_t(int sms, const stream::StreamParams &p, cudaStream_t s) {
     static int per_sm = 0;  // co-resident blocks per SM (cooperative launch bound)
     const size_t smem = sizeof(stream::StreamSmem);
     if (per_sm == 0) {
@@ -222,25 +222,25 @@ cudaError_t launch_stream_t(epsm_ctx *c, const stream::StreamParams &p, cudaStre
         per_sm = std::max(1, std::min(b, stream::kMaxBlocksPerSm));
     }
     const unsigned grid = (unsigned)std::min<uint64_t>(std::max<uint64_t>(p.nstages, 1u),
-                                                       (uint64_t)c->sms * per_sm);
+                                                       (uint64_t)sms * per_sm);
     void *args[] = {(void *)&p};
     return cudaLaunchCooperativeKernel((const void *)stream_kernel<V, MP>, dim3(grid),
                                        dim3(stream::kThreadsStream), args, smem, s);
 }
 
-cudaError_t launch_stream(epsm_ctx *c, int v, uint32_t m, const stream::StreamParams &p,
+cudaError_t launch_stream(int sms, int v, uint32_t m, const stream::StreamParams &p,
                           cudaStream_t s) {
     switch (v) {
         case V_DIRECT:
             switch (m) {
-                case 1: return launch_stream_t<V_DIRECT, 1>(c, p, s);
-                case 2: return launch_stream_t<V_DIRECT, 2>(c, p, s);
-                case 3: return launch_stream_t<V_DIRECT, 3>(c, p, s);
-                default: return launch_stream_t<V_DIRECT, 4>(c, p, s);
+                case 1: return launch_stream_t<V_DIRECT, 1>(sms, p, s);
+                case 2: return launch_stream_t<V_DIRECT, 2>(sms, p, s);
+                case 3: return launch_stream_t<V_DIRECT, 3>(sms, p, s);
+                default: return launch_stream_t<V_DIRECT, 4>(sms, p, s);
             }
-        case V_PREFIX4: return launch_stream_t<V_PREFIX4, 4>(c, p, s);
-        case V_PREFIX8: return launch_stream_t<V_PREFIX8, 8>(c, p, s);
-        default: return launch_stream_t<V_BLOCK8, 8>(c, p, s);
+        case V_PREFIX4: return launch_stream_t<V_PREFIX4, 4>(sms, p, s);
+        case V_PREFIX8: return launch_stream_t<V_PREFIX8, 8>(sms, p, s);
+        default: return launch_stream_t<V_BLOCK8, 8>(sms, p, s);
     }
 }
 
@@ -287,7 +287,7 @@ epsm_status search_async_impl(epsm_ctx *c, int variant, const uint8_t *text, uin
     p.cta_status = c->status;
     p.err = &c->misc->err;
     p.tag = tag;
-    CK(launch_stream(c, v, m, p, s));
+    CK(launch_stream(c->sms, v, m, p, s));
     c->launches += 1;
     return mark_done(c, s);
 }
@@ -575,3 +575,99 @@ EPSM_API epsm_status epsm_set_variant(epsm_ctx *c, uint32_t m, int variant) {
 }
 
 EPSM_API uint64_t epsm_launch_count(epsm_ctx *c) { return c ? c->launches : 0; }
+
+// ---------------------------------------------------------------------------
+// Search without any allocation (epsm_search_static).
+//
+// For callers that cannot allocate device memory at all: code running where
+// cudaMalloc is forbidden or unavailable (inside a framework that owns every
+// allocation through its own pool, a real-time loop where an allocation could
+// stall or fail, or a plug-in whose host application pre-sizes all memory).
+// The streaming kernel's scratch (segment counts and masks, block status
+// words) lives in the fixed array below instead of in a context.  The array
+// is reserved on every GPU that loads this library until the process exits.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr uint64_t kStaticMaxStages =
+    (EPSM_STATIC_MAX_TEXT + 15u + 7u) / stream::kStageBytes + 1u;
+constexpr uint64_t kStaticMaxSegs = kStaticMaxStages * stream::kConsumerWarps;
+constexpr uint64_t kStaticMaxBlocks = 512;  // status words for up to 512 blocks
+constexpr uint64_t kStaticStatusBytes = kStaticMaxBlocks * kStatusStride * sizeof(uint64_t);
+constexpr uint64_t kStaticCountBytes = kStaticMaxSegs * sizeof(uint32_t);
+constexpr uint64_t kStaticMaskBytes = kStaticMaxSegs * stream::kSegChunks * sizeof(uint16_t);
+constexpr uint64_t kStaticBytes = kStaticStatusBytes + kStaticCountBytes + kStaticMaskBytes;
+
+// In host code `g_static_scratch` only names the symbol; its device address
+// comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) uint8_t g_static_scratch[kStaticBytes];
+
+struct StaticDevice {
+    bool ready = false;
+    uint8_t *base = nullptr;  // device address of g_static_scratch on this device
+    int sms = 0;
+    uint32_t tag = 0;
+};
+
+constexpr int kMaxStaticDevices = 64;
+std::mutex g_static_mu;
+StaticDevice g_static_dev[kMaxStaticDevices];
+
+}  // namespace
+
+EPSM_API epsm_status epsm_search_static(const uint8_t *text, uint64_t n, const uint8_t *pattern,
+                                        uint32_t m, uint64_t *positions, uint64_t capacity,
+                                        uint64_t *result_dev, void *stream) {
+    if (!pattern || !result_dev || m == 0 || m > EPSM_MAX_M) return EPSM_ERR_ARG;
+    if (n > 0 && !text) return EPSM_ERR_ARG;
+    if (capacity > 0 && !positions) return EPSM_ERR_ARG;
+    if (n > EPSM_STATIC_MAX_TEXT) return EPSM_ERR_ARG;  // beyond the fixed scratch
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxStaticDevices)
+        return EPSM_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    StaticDevice &D = g_static_dev[dev];
+    if (!D.ready) {
+        // one-time set-up on this device (the device is current)
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) return EPSM_ERR_CUDA;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return EPSM_ERR_CUDA;
+        if ((uint64_t)sms * stream::kMaxBlocksPerSm > kStaticMaxBlocks) return EPSM_ERR_CUDA;
+        D.base = static_cast<uint8_t *>(ptr);
+        D.sms = sms;
+        D.tag = 0;
+        D.ready = true;
+    }
+    // result_dev[0] = count, result_dev[1] = device error bits; the error word
+    // must start at zero
+    if (cudaMemsetAsync(result_dev, 0, 2 * sizeof(uint64_t), s) != cudaSuccess) return EPSM_ERR_CUDA;
+    const int v = default_variant(m);
+    if (n < m) return EPSM_OK;
+    // a fresh tag per call; when tags wrap, stale status words are cleared
+    D.tag = D.tag % kTagMax + 1u;
+    if (D.tag == 1u &&
+        cudaMemsetAsync(D.base, 0, kStaticStatusBytes, s) != cudaSuccess)
+        return EPSM_ERR_CUDA;
+    stream::StreamParams p;
+    memset(&p, 0, sizeof(p));
+    p.job = make_job(text, n, pack_pattern(pattern, m));
+    p.nstages = stages_for(p.job.delta, n, m, v);
+    if (p.nstages > kStaticMaxStages) return EPSM_ERR_ARG;
+    p.chunk_full0 = (p.job.delta + 15u) / 16u;
+    p.chunk_full1 = p.job.lim / 16u;
+    p.emit = capacity > 0 ? 1 : 0;
+    p.positions = positions;
+    p.capacity = capacity;
+    p.count_out = result_dev;
+    p.cta_status = reinterpret_cast<uint64_t *>(D.base);
+    p.seg_count = reinterpret_cast<uint32_t *>(D.base + kStaticStatusBytes);
+    p.seg_mask = reinterpret_cast<uint16_t *>(D.base + kStaticStatusBytes + kStaticCountBytes);
+    p.err = reinterpret_cast<uint32_t *>(result_dev + 1);
+    p.tag = D.tag;
+    if (launch_stream(D.sms, v, m, p, s) != cudaSuccess) return EPSM_ERR_CUDA;
+    return EPSM_OK;
+}
