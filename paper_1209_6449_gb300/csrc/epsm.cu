@@ -121,6 +121,7 @@ struct epsm_ctx {
     // streaming-kernel scratch
     uint32_t *seg_count = nullptr;
     uint16_t *seg_mask = nullptr;
+    unsigned long long *range_total = nullptr;
     uint64_t seg_cap = 0;
     // host end-to-end staging
     uint8_t *dtext = nullptr;
@@ -178,8 +179,10 @@ epsm_status ensure_status(epsm_ctx *c, uint64_t ntiles, cudaStream_t s) {
 // Scratch of the streaming kernel: one count per 2 KiB segment and 128 chunk
 // masks (256 B) per segment, i.e. n/512 + n/8 bytes; status words for the blocks.
 epsm_status ensure_stream_scratch(epsm_ctx *c, uint64_t nstages, cudaStream_t s) {
-    epsm_status st = ensure_status(c, (uint64_t)std::max(c->sms, 1) * stream::kMaxBlocksPerSm, s);
-    if (st != EPSM_OK) return st;
+    if (!c->range_total) {
+        CK(cudaMalloc(&c->range_total, stream::kMaxBlocks * sizeof(unsigned long long)));
+        CK(cudaMemsetAsync(c->range_total, 0, stream::kMaxBlocks * sizeof(unsigned long long), s));
+    }
     const uint64_t nseg = nstages * stream::kConsumerWarps;
     if (nseg <= c->seg_cap) return EPSM_OK;
     uint64_t cap = std::max<uint64_t>(nseg, c->seg_cap * 2);
@@ -208,7 +211,7 @@ epsm_status next_tag(epsm_ctx *c, cudaStream_t s, uint32_t *tag) {
 // Single searches run the cooperative streaming kernel (epsm_stream.cuh): one
 // block per SM, all co-resident.
 template <int V, int MP>
-cudaError_t launch_stream_t(int sms, const stream::StreamParams &p, cudaStream_t s) {
+cudaError_t launch_stream_t(int sms, stream::StreamParams &p, cudaStream_t s) {
     static int per_sm = 0;  // co-resident blocks per SM (cooperative launch bound)
     const size_t smem = sizeof(stream::StreamSmem);
     if (per_sm == 0) {
@@ -221,14 +224,16 @@ cudaError_t launch_stream_t(int sms, const stream::StreamParams &p, cudaStream_t
         if (e != cudaSuccess) return e;
         per_sm = std::max(1, std::min(b, stream::kMaxBlocksPerSm));
     }
-    const unsigned grid = (unsigned)std::min<uint64_t>(std::max<uint64_t>(p.nstages, 1u),
-                                                       (uint64_t)sms * per_sm);
+    uint64_t grid = std::min<uint64_t>(std::max<uint64_t>(p.nstages, 1u), (uint64_t)sms * per_sm);
+    grid = std::min<uint64_t>(grid, stream::kMaxBlocks);
+    // emit ranges of R stages; every block owns one range (possibly empty)
+    p.range_stages = std::max<uint64_t>(1, (p.nstages + grid - 1) / grid);
     void *args[] = {(void *)&p};
     return cudaLaunchCooperativeKernel((const void *)stream_kernel<V, MP>, dim3(grid),
                                        dim3(stream::kThreadsStream), args, smem, s);
 }
 
-cudaError_t launch_stream(int sms, int v, uint32_t m, const stream::StreamParams &p,
+cudaError_t launch_stream(int sms, int v, uint32_t m, stream::StreamParams &p,
                           cudaStream_t s) {
     switch (v) {
         case V_DIRECT:
@@ -277,16 +282,14 @@ epsm_status search_async_impl(epsm_ctx *c, int variant, const uint8_t *text, uin
     p.emit = capacity > 0 ? 1 : 0;
     (void)pos_bias;
     if ((st = ensure_stream_scratch(c, p.nstages, s)) != EPSM_OK) return st;
-    uint32_t tag = 0;
-    if ((st = next_tag(c, s, &tag)) != EPSM_OK) return st;
     p.positions = positions;
     p.capacity = capacity;
     p.count_out = count_dev;
     p.seg_count = c->seg_count;
     p.seg_mask = c->seg_mask;
-    p.cta_status = c->status;
+    p.range_total = c->range_total;
     p.err = &c->misc->err;
-    p.tag = tag;
+    p.misc = c->misc;
     CK(launch_stream(c->sms, v, m, p, s));
     c->launches += 1;
     return mark_done(c, s);
@@ -430,6 +433,7 @@ EPSM_API epsm_status epsm_destroy(epsm_ctx *c) {
     if (c->hoffsets) cudaFreeHost(c->hoffsets);
     if (c->doffsets) cudaFree(c->doffsets);
     if (c->seg_count) cudaFree(c->seg_count);
+    if (c->range_total) cudaFree(c->range_total);
     if (c->seg_mask) cudaFree(c->seg_mask);
     if (c->dtext) cudaFree(c->dtext);
     if (c->dpos) cudaFree(c->dpos);
@@ -593,11 +597,10 @@ namespace {
 constexpr uint64_t kStaticMaxStages =
     (EPSM_STATIC_MAX_TEXT + 15u + 7u) / stream::kStageBytes + 1u;
 constexpr uint64_t kStaticMaxSegs = kStaticMaxStages * stream::kConsumerWarps;
-constexpr uint64_t kStaticMaxBlocks = 512;  // status words for up to 512 blocks
-constexpr uint64_t kStaticStatusBytes = kStaticMaxBlocks * kStatusStride * sizeof(uint64_t);
 constexpr uint64_t kStaticCountBytes = kStaticMaxSegs * sizeof(uint32_t);
 constexpr uint64_t kStaticMaskBytes = kStaticMaxSegs * stream::kSegChunks * sizeof(uint16_t);
-constexpr uint64_t kStaticBytes = kStaticStatusBytes + kStaticCountBytes + kStaticMaskBytes;
+constexpr uint64_t kStaticMiscBytes = 256 + stream::kMaxBlocks * 8;  // DevMisc + range totals
+constexpr uint64_t kStaticBytes = kStaticMiscBytes + kStaticCountBytes + kStaticMaskBytes;
 
 // In host code `g_static_scratch` only names the symbol; its device address
 // comes from cudaGetSymbolAddress, once per device.
@@ -605,9 +608,9 @@ static __device__ __align__(256) uint8_t g_static_scratch[kStaticBytes];
 
 struct StaticDevice {
     bool ready = false;
-    uint8_t *base = nullptr;  // device address of g_static_scratch on this device
+    uint8_t *base = nullptr;  // device address of g_static_scratch on this device, past misc
+    DevMisc *misc = nullptr;
     int sms = 0;
-    uint32_t tag = 0;
 };
 
 constexpr int kMaxStaticDevices = 64;
@@ -636,10 +639,12 @@ EPSM_API epsm_status epsm_search_static(const uint8_t *text, uint64_t n, const u
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return EPSM_ERR_CUDA;
-        if ((uint64_t)sms * stream::kMaxBlocksPerSm > kStaticMaxBlocks) return EPSM_ERR_CUDA;
-        D.base = static_cast<uint8_t *>(ptr);
+        // the claim ticket, done and barrier counters and the range totals
+        // must start at zero
+        if (cudaMemsetAsync(ptr, 0, kStaticMiscBytes, s) != cudaSuccess) return EPSM_ERR_CUDA;
+        D.base = static_cast<uint8_t *>(ptr) + kStaticMiscBytes;
+        D.misc = static_cast<DevMisc *>(ptr);
         D.sms = sms;
-        D.tag = 0;
         D.ready = true;
     }
     // result_dev[0] = count, result_dev[1] = device error bits; the error word
@@ -647,11 +652,6 @@ EPSM_API epsm_status epsm_search_static(const uint8_t *text, uint64_t n, const u
     if (cudaMemsetAsync(result_dev, 0, 2 * sizeof(uint64_t), s) != cudaSuccess) return EPSM_ERR_CUDA;
     const int v = default_variant(m);
     if (n < m) return EPSM_OK;
-    // a fresh tag per call; when tags wrap, stale status words are cleared
-    D.tag = D.tag % kTagMax + 1u;
-    if (D.tag == 1u &&
-        cudaMemsetAsync(D.base, 0, kStaticStatusBytes, s) != cudaSuccess)
-        return EPSM_ERR_CUDA;
     stream::StreamParams p;
     memset(&p, 0, sizeof(p));
     p.job = make_job(text, n, pack_pattern(pattern, m));
@@ -663,11 +663,11 @@ EPSM_API epsm_status epsm_search_static(const uint8_t *text, uint64_t n, const u
     p.positions = positions;
     p.capacity = capacity;
     p.count_out = result_dev;
-    p.cta_status = reinterpret_cast<uint64_t *>(D.base);
-    p.seg_count = reinterpret_cast<uint32_t *>(D.base + kStaticStatusBytes);
-    p.seg_mask = reinterpret_cast<uint16_t *>(D.base + kStaticStatusBytes + kStaticCountBytes);
+    p.seg_count = reinterpret_cast<uint32_t *>(D.base);
+    p.seg_mask = reinterpret_cast<uint16_t *>(D.base + kStaticCountBytes);
     p.err = reinterpret_cast<uint32_t *>(result_dev + 1);
-    p.tag = D.tag;
+    p.misc = D.misc;
+    p.range_total = reinterpret_cast<unsigned long long *>(reinterpret_cast<uint8_t *>(D.misc) + 256);
     if (launch_stream(D.sms, v, m, p, s) != cudaSuccess) return EPSM_ERR_CUDA;
     return EPSM_OK;
 }

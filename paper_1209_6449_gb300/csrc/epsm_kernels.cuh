@@ -10,11 +10,11 @@ namespace epsm {
 // tiles already claimed by running blocks), a "done" counter (the last block
 // to finish resets both for the next launch), the error word and a count slot.
 struct DevMisc {
-    uint64_t count;   // count slot for the synchronous entry points
-    uint32_t ticket;
-    uint32_t done;
-    uint32_t err;
-    uint32_t pad;
+    uint64_t count;    // count slot for the synchronous entry points
+    uint32_t ticket;   // next work unit to claim
+    uint32_t done;     // blocks that have finished
+    uint32_t err;      // device error bits
+    uint32_t barrier;  // arrivals at the streaming kernel's grid barrier
 };
 
 __device__ __forceinline__ uint32_t claim_tile(DevMisc *misc) { return atomicAdd(&misc->ticket, 1u); }
@@ -27,6 +27,7 @@ __device__ __forceinline__ void finish_claims(DevMisc *misc) {
     if (d == gridDim.x - 1u) {
         misc->ticket = 0u;
         misc->done = 0u;
+        misc->barrier = 0u;
         __threadfence();
     }
 }

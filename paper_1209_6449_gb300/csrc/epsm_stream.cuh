@@ -1,24 +1,28 @@
-// Streaming scan: filter pass, one cross-block prefix, emit pass — in one
-// cooperative persistent launch (up to two blocks per SM, all co-resident).
+// Streaming scan: filter pass, grid barrier, per-block prefix, emit pass —
+// in one cooperative persistent launch (up to two blocks per SM, all
+// co-resident).
 //
 // The text is cut into 16 KiB stages (1024 chunks of 16 bytes) and each stage
-// into 8 segments of 128 chunks (2 KiB), one per consumer warp.  Block b owns a
-// contiguous run of stages, so positions found by block b all precede those
-// of block b+1, and inside a block the stages are handled in order.
+// into 8 segments of 128 chunks (2 KiB), one per consumer warp.
 //
-// Phase 1 (no waiting on other blocks).  A producer warp streams the block's
-// stages through a ring of shared-memory buffers with 1-D bulk copies
-// (cp.async.bulk, completion on an mbarrier), keeping up to kStages x 16 KiB of
-// reads in flight.  Each consumer warp runs the variant's filter and verify
-// (chunk_hits) on its segment of the staged stage, writes the segment's hit
-// count, and, only if the segment has hits, its 128 16-bit chunk masks to
-// scratch memory.
-// Phase 2.  The block publishes its total; one warp sums the totals of all
-// earlier blocks (decoupled look-back over at most #SM words, one round).
-// Phase 3.  Consumer warps prefix-sum the segment counts of the block in
-// order and emit the positions of every segment with hits: offsets of the
-// segment's hits are staged in shared memory in output order, then written as
-// consecutive 8-byte positions (coalesced stores).
+// Phase 1 (no ordering, no waiting on other blocks).  A producer warp claims
+// stages in batches from a global ticket (the next claim is requested while
+// the current batch is issued) and streams them through a ring of
+// shared-memory buffers with 1-D bulk copies (cp.async.bulk, completion on an
+// mbarrier), keeping up to kStages x 16 KiB of reads in flight per block.
+// Each consumer warp runs the variant's filter and verify (chunk_hits) on its
+// segment of each staged stage and writes the segment's hit count and, only if
+// it has hits, its 128 16-bit chunk masks to scratch.  Dynamic claiming keeps
+// every SM busy until the text is exhausted (a static split left the slowest
+// block ~40% behind the fastest).
+// Grid barrier (bounded).  All counts and masks are then written.
+// Phase 2.  Block b owns the emit range of stages [b*R, (b+1)*R).  The hit
+// total of every range was accumulated in phase 1; one warp sums the totals
+// of the ranges before the block's own (one round of loads).
+// Phase 3.  Consumer warps prefix-sum the segment counts of the range in order
+// and emit the positions of every segment with hits: the hit offsets are
+// staged in shared memory in output order, then written as consecutive 8-byte
+// positions (coalesced stores).
 //
 // Every wait is bounded in time; on expiry the error word gets kErrTimeout and
 // the waiting warp gives up, so the kernel always ends.  The producer waits,
@@ -40,15 +44,19 @@ constexpr int kSegChunks = 128;                             // chunks per segmen
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kConsumerBarrier = 1;                         // named barrier of consumer warps
 constexpr int kMaxBlocksPerSm = 2;
+constexpr uint64_t kMaxBlocks = 512;                        // grid bound (range totals, status words)
+
+constexpr uint32_t kClaim = 2;                              // stages per claim
+constexpr uint64_t kEndStage = ~0ull;
 
 struct alignas(128) StreamSmem {
     uint8_t buf[kStages][kStageBuf];
+    uint64_t stage_id[kStages];  // global stage held by each ring slot (kEndStage: done)
     uint64_t full[kStages];
     uint64_t empty[kStages];
     uint32_t pblk[16];
     uint8_t table[kHashSlots];
     uint16_t emit_stage[kConsumerWarps][32 * 16];  // per-warp staging of hit offsets
-    uint32_t warp_total[kConsumerWarps];
     uint32_t scan_tmp[kConsumerWarps];
     uint64_t cta_excl;
     uint64_t cta_total;
@@ -77,14 +85,19 @@ __device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t tx) {
                  : "memory");
 }
 
+// try_wait with a suspend-time hint: a waiting thread sleeps until the phase
+// completes (or the hint elapses) instead of spinning, so waiting consumer
+// warps do not take issue slots from the producer.
+constexpr uint32_t kSuspendHintNs = 20000u;
+
 __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendHintNs)
         : "memory");
     return ok != 0u;
 }
@@ -125,12 +138,13 @@ struct StreamParams {
     uint64_t *count_out;   // device: receives the total
     uint32_t *seg_count;   // scratch: hits per segment
     uint16_t *seg_mask;    // scratch: 128 chunk masks per segment with hits
-    uint64_t *cta_status;  // scratch: one status word per block (kStatusStride apart)
     uint32_t *err;
+    DevMisc *misc;         // claim ticket, done counter, grid-barrier counter
+    unsigned long long *range_total;  // scratch: hits per emit range (zero between calls)
+    uint64_t range_stages; // stages per emit range: block b emits [b*R, (b+1)*R)
     uint64_t nstages;      // 16 KiB stages of the text
     uint64_t chunk_full0;  // first chunk lying fully inside [delta, lim)
     uint64_t chunk_full1;  // one past the last such chunk
-    uint32_t tag;          // call tag of the status words
     int emit;              // 0: count only
 };
 
@@ -141,36 +155,56 @@ __device__ __forceinline__ uint4 staged_chunk(const StreamParams &P, const uint8
     return load_chunk(P.job, c);
 }
 
-__device__ __forceinline__ void block_range(uint64_t n, uint64_t *a, uint64_t *b) {
-    *a = n * blockIdx.x / gridDim.x;
-    *b = n * (blockIdx.x + 1) / gridDim.x;
-}
-
 // ---------------------------------------------------------------------------
 // phase 1 roles
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void producer(const StreamParams &P, StreamSmem &S, uint64_t st0,
-                                         uint64_t st1) {
+__device__ __forceinline__ void issue_stage(const StreamParams &P, StreamSmem &S, int s,
+                                            uint64_t st) {
     const SearchJob &J = P.job;
+    S.stage_id[s] = st;
+    const uint64_t c0 = st * kStageChunks;
+    const uint64_t a = c0 > P.chunk_full0 ? c0 : P.chunk_full0;
+    uint64_t b = c0 + kStageChunks + 1u;  // + halo chunk
+    if (b > P.chunk_full1) b = P.chunk_full1;
+    if (a < b) {
+        const uint32_t bytes = (uint32_t)((b - a) * 16u);
+        mbar_arrive_tx(&S.full[s], bytes);
+        bulk_load(S.buf[s] + (a - c0) * 16u, J.base + a * 16u, bytes, &S.full[s]);
+    } else {
+        mbar_arrive(&S.full[s]);
+    }
+}
+
+// Producer (one thread): claims batches of kClaim stages and issues them; the
+// claim of the next batch is requested before the current batch is issued so
+// that its latency overlaps the copies.  When a claim comes back past the end
+// of the text, the next ring slot is marked kEndStage.
+__device__ __forceinline__ void producer(const StreamParams &P, StreamSmem &S) {
     uint32_t issued = 0;
     bool failed = false;
-    for (uint64_t st = st0; st < st1; ++st) {
-        const int s = issued % kStages;
-        const uint32_t n = issued / kStages;
-        if (n > 0 && !mbar_wait(&S.empty[s], (n - 1) & 1)) { failed = true; break; }
-        const uint64_t c0 = st * kStageChunks;
-        const uint64_t a = c0 > P.chunk_full0 ? c0 : P.chunk_full0;
-        uint64_t b = c0 + kStageChunks + 1u;  // + halo chunk
-        if (b > P.chunk_full1) b = P.chunk_full1;
-        if (a < b) {
-            const uint32_t bytes = (uint32_t)((b - a) * 16u);
-            mbar_arrive_tx(&S.full[s], bytes);
-            bulk_load(S.buf[s] + (a - c0) * 16u, J.base + a * 16u, bytes, &S.full[s]);
-        } else {
+    uint64_t claim = atomicAdd(&P.misc->ticket, kClaim);
+    for (;;) {
+        if (claim >= P.nstages) {
+            const int s = issued % kStages;
+            const uint32_t n = issued / kStages;
+            if (n > 0 && !mbar_wait(&S.empty[s], (n - 1) & 1)) { failed = true; break; }
+            S.stage_id[s] = kEndStage;
             mbar_arrive(&S.full[s]);
+            ++issued;
+            break;
         }
-        ++issued;
+        const uint64_t next = atomicAdd(&P.misc->ticket, kClaim);
+        const uint64_t last = claim + kClaim < P.nstages ? claim + kClaim : P.nstages;
+        for (uint64_t st = claim; st < last; ++st) {
+            const int s = issued % kStages;
+            const uint32_t n = issued / kStages;
+            if (n > 0 && !mbar_wait(&S.empty[s], (n - 1) & 1)) { failed = true; break; }
+            issue_stage(P, S, s, st);
+            ++issued;
+        }
+        if (failed) break;
+        claim = next;
     }
     if (failed) atomicOr(P.err, kErrTimeout);
     // Leave no copy in flight: wait (bounded) for the last issued stages.
@@ -186,17 +220,18 @@ __device__ __noinline__ uint4 edge_chunk(const StreamParams &P, const uint8_t *b
 }
 
 template <int V, int MP>
-__device__ __forceinline__ uint32_t filter_stages(const StreamParams &P, StreamSmem &S, uint64_t st0,
-                                                  uint64_t st1, int w, int lane, bool *ok) {
+__device__ __forceinline__ void filter_stages(const StreamParams &P, StreamSmem &S, int w, int lane,
+                                              bool *ok) {
     constexpr int OFF = (V == V_BLOCK8) ? -7 : 0;
     const SearchJob &J = P.job;
     const BcastWords B(J.pat);
-    uint32_t total = 0u;
-    uint32_t i = 0;
     const uint32_t lane_off = (uint32_t)(w * kSegChunks + lane) * 16u;  // byte offset in a stage
-    for (uint64_t st = st0; st < st1; ++st, ++i) {
-        const int s = i % kStages;
-        if (!warp_wait(&S.full[s], (i / kStages) & 1)) { *ok = false; break; }
+    int s = 0;
+    uint32_t phase = 0;
+    for (;;) {
+        if (!warp_wait(&S.full[s], phase)) { *ok = false; break; }
+        const uint64_t st = S.stage_id[s];
+        if (st == kEndStage) break;
         const uint64_t c0 = st * kStageChunks;
         const uint8_t *buf = S.buf[s];
         // stage entirely inside the text (all but the first and last stages):
@@ -234,56 +269,105 @@ __device__ __forceinline__ uint32_t filter_stages(const StreamParams &P, StreamS
         // the stage buffer is no longer needed: release it to the producer
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[s]);
-        const uint32_t wc = warp_sum(cnt);
+        if (++s == kStages) { s = 0; phase ^= 1u; }
+        const uint32_t wc = __any_sync(kFull, cnt != 0u) ? warp_sum(cnt) : 0u;
         const uint64_t seg = st * kConsumerWarps + (uint64_t)w;
-        if (lane == 0) P.seg_count[seg] = wc;
-        if (wc != 0u && P.emit) {
-            uint16_t *mk = P.seg_mask + seg * kSegChunks;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) mk[u * 32 + lane] = (uint16_t)h[u];
+        if (lane == 0) {
+            P.seg_count[seg] = wc;
+            if (wc) atomicAdd(&P.range_total[st / P.range_stages], (unsigned long long)wc);
         }
-        total += wc;
+        if (wc != 0u && P.emit) {
+            // lane-major: lane l's four chunk masks are one 8-byte word
+            uint2 packed;
+            packed.x = (h[0] & 0xFFFFu) | (h[1] << 16);
+            packed.y = (h[2] & 0xFFFFu) | (h[3] << 16);
+            reinterpret_cast<uint2 *>(P.seg_mask + seg * kSegChunks)[lane] = packed;
+        }
     }
-    return total;
 }
 
-// Emit the positions of one segment (a whole warp): bit b of the mask of
-// chunk c is the start 16*c + OFF + b.
+// Emit the positions of one segment (a whole warp), given lane l's packed
+// masks (chunks 32u + l, u = 0..3): bit b of the mask of chunk c is the start
+// 16*c + OFF + b.  The four per-step warp scans run interleaved; the hits are
+// staged in shared memory as offsets inside the segment, in output order, and
+// written as consecutive 8-byte positions — in one pass when they fit in the
+// 512-entry stage (the common case), else one pass per step.
 template <int OFF>
 __device__ __forceinline__ void emit_segment(const StreamParams &P, uint64_t seg, uint64_t idx0,
-                                             uint16_t *stage, int lane) {
+                                             uint2 packed, uint16_t *stage, int lane) {
     const SearchJob &J = P.job;
-    const uint16_t *mk = P.seg_mask + seg * kSegChunks;
-    uint32_t run = 0u;
+    uint32_t h[4], c[4], inc[4], T[4];
+    h[0] = packed.x & 0xFFFFu;
+    h[1] = packed.x >> 16;
+    h[2] = packed.y & 0xFFFFu;
+    h[3] = packed.y >> 16;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const uint32_t h = mk[u * 32 + lane];
-        const uint32_t c = __popc(h);
-        if (!__any_sync(kFull, c != 0u)) continue;
-        const uint32_t inc = warp_incl_scan(c, lane);
-        const uint32_t T = __shfl_sync(kFull, inc, 31);
-        uint32_t k = inc - c;
-        uint32_t hh = h;
-        while (hh) {
-            const uint32_t b = (uint32_t)(__ffs(hh) - 1);
-            hh &= hh - 1u;
-            stage[k++] = (uint16_t)(lane * 16 + b);
+        c[u] = __popc(h[u]);
+        inc[u] = c[u];
+    }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t t = __shfl_up_sync(kFull, inc[u], d);
+            if (lane >= d) inc[u] += t;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) T[u] = __shfl_sync(kFull, inc[u], 31);
+    const uint32_t total = T[0] + T[1] + T[2] + T[3];
+    const int64_t s0 = (int64_t)(seg * kSegChunks * 16u) + OFF - (int64_t)J.delta;
+    if (lane == 0 && idx0 + total > P.capacity) atomicOr(P.err, kErrCapacity);
+    if (total <= 32u * 16u) {
+        uint32_t before = 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            uint32_t k = before + inc[u] - c[u];
+            uint32_t hh = h[u];
+            while (hh) {
+                const uint32_t b = (uint32_t)(__ffs(hh) - 1);
+                hh &= hh - 1u;
+                stage[k++] = (uint16_t)(u * 512 + lane * 16 + b);
+            }
+            before += T[u];
         }
         __syncwarp();
-        const int64_t s0 = (int64_t)((seg * kSegChunks + 32u * u) * 16u) + OFF - (int64_t)J.delta;
-        const uint64_t base = idx0 + run;
-        if (lane == 0 && base + T > P.capacity) atomicOr(P.err, kErrCapacity);
-        for (uint32_t q = lane; q < T; q += 32u) {
-            const uint64_t idx = base + q;
+        for (uint32_t q = lane; q < total; q += 32u) {
+            const uint64_t idx = idx0 + q;
             if (idx < P.capacity) P.positions[idx] = (uint64_t)(s0 + stage[q]);
         }
         __syncwarp();
-        run += T;
+        return;
+    }
+    uint32_t run = 0u;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        uint32_t k = inc[u] - c[u];
+        uint32_t hh = h[u];
+        while (hh) {
+            const uint32_t b = (uint32_t)(__ffs(hh) - 1);
+            hh &= hh - 1u;
+            stage[k++] = (uint16_t)(u * 512 + lane * 16 + b);
+        }
+        __syncwarp();
+        for (uint32_t q = lane; q < T[u]; q += 32u) {
+            const uint64_t idx = idx0 + run + q;
+            if (idx < P.capacity) P.positions[idx] = (uint64_t)(s0 + stage[q]);
+        }
+        __syncwarp();
+        run += T[u];
     }
 }
 
+__device__ __forceinline__ uint2 load_masks(const StreamParams &P, uint64_t seg, int lane) {
+    return reinterpret_cast<const uint2 *>(P.seg_mask + seg * kSegChunks)[lane];
+}
+
 // Phase 3 for the consumer warps: block-ordered prefix of the segment counts
-// in batches of 256 segments, and emission of the segments with hits.
+// in batches of 256 segments, and emission of the segments with hits.  Each
+// warp walks its segments with hits and loads the next one's masks before it
+// emits the current one, so mask loads overlap the stores.
 template <int OFF>
 __device__ __forceinline__ void emit_block(const StreamParams &P, StreamSmem &S, uint64_t st0,
                                            uint64_t st1, int w, int lane) {
@@ -306,42 +390,64 @@ __device__ __forceinline__ void emit_block(const StreamParams &P, StreamSmem &S,
         consumer_sync();
         const uint64_t excl = base + wbase + inc - c;
         uint32_t todo = __ballot_sync(kFull, c != 0u);
-        while (todo) {
-            const int j = __ffs(todo) - 1;
+        if (todo) {
+            int j = __ffs(todo) - 1;
             todo &= todo - 1u;
-            const uint64_t sj = sb + (uint64_t)w * 32u + (uint64_t)j;
-            const uint64_t ej = __shfl_sync(kFull, excl, j);
-            emit_segment<OFF>(P, sj, ej, S.emit_stage[w], lane);
+            uint64_t sj = sb + (uint64_t)w * 32u + (uint64_t)j;
+            uint2 cur = load_masks(P, sj, lane);
+            for (;;) {
+                const uint64_t ej = __shfl_sync(kFull, excl, j);
+                int jn = -1;
+                uint64_t sn = 0;
+                uint2 nxt = make_uint2(0u, 0u);
+                if (todo) {
+                    jn = __ffs(todo) - 1;
+                    todo &= todo - 1u;
+                    sn = sb + (uint64_t)w * 32u + (uint64_t)jn;
+                    nxt = load_masks(P, sn, lane);
+                }
+                emit_segment<OFF>(P, sj, ej, cur, S.emit_stage[w], lane);
+                if (jn < 0) break;
+                j = jn;
+                sj = sn;
+                cur = nxt;
+            }
         }
         base += btotal;
     }
 }
 
-// Sum of the totals of blocks 0..blockIdx.x-1 (one warp).  Every block is
-// resident (cooperative launch), so each waits only for blocks that run.
-__device__ __forceinline__ uint64_t blocks_before(const StreamParams &P, uint64_t mine, int lane,
-                                                  bool *ok) {
-    uint64_t *st = P.cta_status;
-    if (lane == 0)
-        st_relaxed_u64(st + (uint64_t)blockIdx.x * kStatusStride,
-                       pack_status(P.tag, kFlagAgg, mine));
-    uint64_t sum = 0;
-    const uint64_t t0 = globaltimer_ns();
-    for (uint32_t base = 0; base < blockIdx.x; base += 32) {
-        const uint32_t b = base + lane;
-        uint64_t v = 0;
-        if (b < blockIdx.x) {
-            for (;;) {
-                const uint64_t s = ld_relaxed_u64(st + (uint64_t)b * kStatusStride);
-                if ((uint32_t)(s >> kTagShift) == P.tag) { v = s & kValMask; break; }
-                if (globaltimer_ns() - t0 > kWaitNs) { *ok = false; break; }
-                __nanosleep(64);
-            }
-        }
-        sum += warp_sum64(v);
+// The last block to finish resets the claim/barrier counters and zeroes the
+// range totals for the next launch (they are read by all blocks in phase 2,
+// which every block has passed by then).
+__device__ __forceinline__ void finish_stream(const StreamParams &P) {
+    __threadfence();
+    const uint32_t d = atomicAdd(&P.misc->done, 1u);
+    if (d == gridDim.x - 1u) {
+        for (uint32_t b = 0; b < gridDim.x; ++b) P.range_total[b] = 0ull;
+        P.misc->ticket = 0u;
+        P.misc->done = 0u;
+        P.misc->barrier = 0u;
+        __threadfence();
     }
-    *ok = __all_sync(kFull, *ok) != 0;
-    return sum;
+}
+
+// Grid-wide barrier of the co-resident blocks (called by one thread per
+// block, between __syncthreads): bounded wait on an arrival counter that the
+// last block to finish resets.
+__device__ __forceinline__ bool grid_barrier(DevMisc *misc) {
+    __threadfence();
+    atomicAdd(&misc->barrier, 1u);
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        uint32_t v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&misc->barrier) : "memory");
+        if (v >= gridDim.x) break;
+        if (globaltimer_ns() - t0 > kWaitNs) return false;
+        __nanosleep(128);
+    }
+    __threadfence();
+    return true;
 }
 
 }  // namespace stream
@@ -366,31 +472,39 @@ __global__ void __launch_bounds__(stream::kThreadsStream, stream::kMaxBlocksPerS
     if (V == V_BLOCK8) build_block_table(P.job.pat, S.table, S.pblk);
     __syncthreads();
 
-    uint64_t st0, st1;
-    block_range(P.nstages, &st0, &st1);
-
-    // phase 1: stream and filter
+    // phase 1: stream and filter (stages claimed dynamically)
     bool ok = true;
     if (warp == kConsumerWarps) {
-        if (lane == 0) producer(P, S, st0, st1);
+        if (lane == 0) producer(P, S);
     } else {
-        const uint32_t total = filter_stages<V, MP>(P, S, st0, st1, warp, lane, &ok);
-        if (lane == 0) S.warp_total[warp] = total;
+        filter_stages<V, MP>(P, S, warp, lane, &ok);
         if (!ok && lane == 0) atomicOr(P.err, kErrTimeout);
     }
     __syncthreads();
+    if (threadIdx.x == 0 && !grid_barrier(P.misc)) atomicOr(P.err, kErrTimeout);
+    __syncthreads();
 
-    // phase 2: block total and the totals of all earlier blocks
+    // phase 2: the totals of all emit ranges are final after the barrier; sum
+    // those before this block's range (one round of loads)
+    const uint64_t st0 = (uint64_t)blockIdx.x * P.range_stages;
+    const uint64_t st1 = st0 + P.range_stages < P.nstages ? st0 + P.range_stages : P.nstages;
     if (warp == 0) {
-        uint64_t mine = 0;
-        for (int k = 0; k < kConsumerWarps; ++k) mine += S.warp_total[k];
-        bool bok = true;
-        const uint64_t before = blocks_before(P, mine, lane, &bok);
+        uint64_t before = 0, all = 0;
+        for (uint32_t b = lane; b < gridDim.x; b += 32) {
+            const uint64_t v = ld_relaxed_u64(reinterpret_cast<const uint64_t *>(P.range_total) + b);
+            all += v;
+            if (b < blockIdx.x) before += v;
+        }
+        before = warp_sum64(before);
+        all = warp_sum64(all);
         if (lane == 0) {
-            if (!bok) atomicOr(P.err, kErrTimeout);
             S.cta_excl = before;
+            S.cta_total = 0;
+        }
+        const uint64_t mine = ld_relaxed_u64(reinterpret_cast<const uint64_t *>(P.range_total) + blockIdx.x);
+        if (lane == 0) {
             S.cta_total = mine;
-            if (blockIdx.x + 1 == gridDim.x) *P.count_out = before + mine;
+            if (blockIdx.x + 1 == gridDim.x) *P.count_out = all;
         }
     }
     __syncthreads();
@@ -398,6 +512,8 @@ __global__ void __launch_bounds__(stream::kThreadsStream, stream::kMaxBlocksPerS
     // phase 3: ordered emit
     if (P.emit && warp < kConsumerWarps && S.cta_total != 0ull)
         emit_block<OFF>(P, S, st0, st1, warp, lane);
+    __syncthreads();
+    if (threadIdx.x == 0) finish_stream(P);
 }
 
 }  // namespace epsm
