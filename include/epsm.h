@@ -109,8 +109,7 @@ epsm_status epsm_search_variant(epsm_ctx *ctx, int variant, const uint8_t *text,
 epsm_status epsm_sync(epsm_ctx *ctx, void *stream);
 
 /* Batched search over `npairs` independent (text, pattern) pairs of uneven n
- * and m, in one persistent launch (north of the paper: each pair is one
- * Section 1 problem).
+ * and m, in one persistent launch (each pair is one Section 1 problem).
  *   texts      host array of npairs DEVICE text pointers
  *   ns         host array of npairs text lengths
  *   patterns   host array of npairs HOST pattern pointers
@@ -148,6 +147,11 @@ epsm_status epsm_set_variant(epsm_ctx *ctx, uint32_t m, int variant);
 
 /* Number of kernel launches the context has issued (all entry points). */
 uint64_t epsm_launch_count(epsm_ctx *ctx);
+
+/* 1 if the context's batched submissions replay a captured CUDA graph
+ * (upload, pattern-table build, batched scan, offsets download), 0 if they are
+ * launched directly (no batch run yet, or graph capture unavailable). */
+int epsm_batch_uses_graph(epsm_ctx *ctx);
 
 /* Largest text epsm_search_static accepts (bytes). */
 #define EPSM_STATIC_MAX_TEXT (64ull << 20)

@@ -260,3 +260,7 @@ class Context:
     @property
     def launch_count(self) -> int:
         return epsm_launch_count(self.handle)
+
+    @property
+    def batch_uses_graph(self) -> bool:
+        return bool(_lib.epsm_batch_uses_graph(self.handle))

@@ -21,7 +21,7 @@ MAX_M = 32
 EXPORTS = ["epsm_create", "epsm_destroy", "epsm_status_str", "epsm_last_error",
            "epsm_search", "epsm_search_async", "epsm_search_variant", "epsm_sync",
            "epsm_search_batch", "epsm_search_host", "epsm_variant_for", "epsm_set_variant",
-           "epsm_launch_count", "epsm_search_static"]
+           "epsm_launch_count", "epsm_search_static", "epsm_batch_uses_graph"]
 STATIC_MAX_TEXT = 64 << 20
 
 
@@ -68,6 +68,8 @@ def load(path: str | None = None):
     lib.epsm_set_variant.restype = st
     lib.epsm_launch_count.argtypes = [vp]
     lib.epsm_launch_count.restype = u64
+    lib.epsm_batch_uses_graph.argtypes = [vp]
+    lib.epsm_batch_uses_graph.restype = i32
     lib.epsm_search_static.argtypes = [vp, u64, vp, u32, vp, u64, vp, vp]
     lib.epsm_search_static.restype = st
     if path is None:

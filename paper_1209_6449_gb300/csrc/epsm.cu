@@ -20,16 +20,13 @@
 #include "epsm.h"
 #include "epsm_kernels.cuh"
 #include "epsm_stream.cuh"
+#include "epsm_batch.cuh"
 
 using namespace epsm;
 
 #define EPSM_API extern "C" __attribute__((visibility("default")))
 
 namespace {
-
-constexpr int kDefaultU = 4;                          // chunks per lane per tile
-constexpr uint64_t kTileBytes = (uint64_t)kThreads * kDefaultU * 16u;  // 16 KiB
-constexpr uint32_t kTagMax = (1u << 22) - 1u;
 
 int default_variant(uint32_t m) {
     if (m <= 3) return V_DIRECT;
@@ -49,13 +46,6 @@ bool variant_covers(int v, uint32_t m) {
 }
 
 int variant_offset(int v) { return v == V_BLOCK8 ? -7 : 0; }
-
-// Tiles needed for a job: tile t covers starts [t*T + OFF, (t+1)*T + OFF).
-uint64_t tiles_for(uint64_t delta, uint64_t n, uint32_t m, int v) {
-    if (n < m || n == 0) return 0;
-    int64_t pmax = (int64_t)(delta + n - m);
-    return (uint64_t)((pmax - variant_offset(v)) / (int64_t)kTileBytes) + 1u;
-}
 
 Pattern pack_pattern(const uint8_t *p, uint32_t m) {
     Pattern pat;
@@ -81,18 +71,27 @@ SearchJob make_job(const uint8_t *text, uint64_t n, const Pattern &pat) {
     return J;
 }
 
-std::mutex g_occ_mu;
-std::unordered_map<const void *, int> g_occ;
+// Per-context resources of the batched launch: one pinned staging buffer
+// holding the header and the job table, device copies of both, the
+// fingerprint tables, the job offsets, and the CUDA graph of the submission
+// (header/jobs upload -> table build -> batched scan -> offsets download),
+// built once per capacity and replayed for every batch that fits.
+struct BatchRes {
+    uint8_t *hstage = nullptr;  // pinned: Header, then JobDesc[cap]
+    uint8_t *dstage = nullptr;
+    uint64_t *hoff = nullptr;   // pinned: job offsets + total
+    uint64_t *doff = nullptr;
+    uint8_t *tables = nullptr;
+    uint32_t cap = 0;           // jobs
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t up = nullptr, down = nullptr;
+    uint64_t graph_seg_cap = 0;      // scratch size the graph was built with
+    uint64_t *graph_positions = nullptr;
+    bool graph_failed = false;       // a build failed once: launch directly
+    int grid = 0;
+};
 
-int blocks_per_sm(const void *fn) {
-    std::lock_guard<std::mutex> lk(g_occ_mu);
-    auto it = g_occ.find(fn);
-    if (it != g_occ.end()) return it->second;
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kThreads, 0) != cudaSuccess || b < 1) b = 1;
-    g_occ[fn] = b;
-    return b;
-}
+constexpr size_t kBatchHdrBytes = 64;  // Header, padded to keep JobDesc aligned
 
 }  // namespace
 
@@ -102,22 +101,14 @@ struct epsm_ctx {
     int sms = 0;
     DevMisc *misc = nullptr;     // device
     DevMisc *hmisc = nullptr;    // pinned host mirror
-    uint64_t *status = nullptr;  // look-back status words
-    uint64_t status_cap = 0;
-    uint32_t epoch = 0;
     cudaEvent_t ev = nullptr;
     cudaStream_t last_stream = nullptr;
     bool have_ev = false;
     int variant[EPSM_MAX_M + 1];
     uint64_t launches = 0;
     char errbuf[256];
-    // batch staging
-    BatchPair *hpairs = nullptr;
-    BatchPair *dpairs = nullptr;
-    uint32_t pairs_cap = 0;
-    uint64_t *hoffsets = nullptr;
-    uint64_t *doffsets = nullptr;
-    uint32_t offsets_cap = 0;
+    // batched launch
+    BatchRes batch;
     // streaming-kernel scratch
     uint32_t *seg_count = nullptr;
     uint16_t *seg_mask = nullptr;
@@ -163,18 +154,6 @@ epsm_status mark_done(epsm_ctx *c, cudaStream_t s) {
     return EPSM_OK;
 }
 
-epsm_status ensure_status(epsm_ctx *c, uint64_t ntiles, cudaStream_t s) {
-    if (ntiles <= c->status_cap) return EPSM_OK;
-    uint64_t cap = std::max<uint64_t>(ntiles, c->status_cap * 2);
-    CK(cudaStreamSynchronize(s));
-    if (c->status) CK(cudaFree(c->status));
-    c->status = nullptr;
-    c->status_cap = 0;
-    CK(cudaMalloc(&c->status, cap * kStatusStride * sizeof(uint64_t)));
-    CK(cudaMemsetAsync(c->status, 0, cap * kStatusStride * sizeof(uint64_t), s));
-    c->status_cap = cap;
-    return EPSM_OK;
-}
 
 // Scratch of the streaming kernel: one count per 2 KiB segment and 128 chunk
 // masks (256 B) per segment, i.e. n/512 + n/8 bytes; status words for the blocks.
@@ -198,15 +177,6 @@ epsm_status ensure_stream_scratch(epsm_ctx *c, uint64_t nstages, cudaStream_t s)
     return EPSM_OK;
 }
 
-epsm_status next_tag(epsm_ctx *c, cudaStream_t s, uint32_t *tag) {
-    c->epoch = c->epoch % kTagMax + 1u;
-    if (c->epoch == 1u && c->status_cap) {
-        // tags wrapped: clear every status word so that no stale word matches
-        CK(cudaMemsetAsync(c->status, 0, c->status_cap * kStatusStride * sizeof(uint64_t), s));
-    }
-    *tag = c->epoch;
-    return EPSM_OK;
-}
 
 // Single searches run the cooperative streaming kernel (epsm_stream.cuh): one
 // block per SM, all co-resident.
@@ -307,20 +277,130 @@ epsm_status read_misc(epsm_ctx *c, cudaStream_t s, uint32_t *err) {
     return EPSM_OK;
 }
 
-template <typename T>
-epsm_status grow_pinned(epsm_ctx *c, T **h, T **d, uint32_t *cap, uint32_t need) {
-    if (need <= *cap) return EPSM_OK;
-    uint32_t nc = std::max<uint32_t>(need, *cap * 2);
+
+void free_batch(BatchRes &R) {
+    if (R.exec) cudaGraphExecDestroy(R.exec);
+    if (R.hstage) cudaFreeHost(R.hstage);
+    if (R.dstage) cudaFree(R.dstage);
+    if (R.hoff) cudaFreeHost(R.hoff);
+    if (R.doff) cudaFree(R.doff);
+    if (R.tables) cudaFree(R.tables);
+    R = BatchRes();
+}
+
+int batch_grid(int sms) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        const size_t smem = sizeof(batch::BatchSmem);
+        if (cudaFuncSetAttribute(batch_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return 0;
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_stream_kernel,
+                                                          stream::kThreadsStream, smem) != cudaSuccess)
+            return 0;
+        per_sm = std::max(1, std::min(b, stream::kMaxBlocksPerSm));
+    }
+    return (int)std::min<uint64_t>((uint64_t)sms * per_sm, stream::kMaxBlocks);
+}
+
+epsm_status ensure_batch(epsm_ctx *c, uint32_t njobs, cudaStream_t s) {
+    BatchRes &R = c->batch;
+    if (R.hstage && njobs <= R.cap) return EPSM_OK;
+    const uint32_t cap = std::max<uint32_t>({njobs, R.cap * 2u, 64u});
+    CK(cudaStreamSynchronize(s));
     CK(cudaDeviceSynchronize());
-    if (*h) CK(cudaFreeHost(*h));
-    if (*d) CK(cudaFree(*d));
-    *h = nullptr;
-    *d = nullptr;
-    *cap = 0;
-    CK(cudaMallocHost((void **)h, sizeof(T) * nc));
-    CK(cudaMalloc((void **)d, sizeof(T) * nc));
-    *cap = nc;
+    free_batch(R);
+    const size_t stage_bytes = kBatchHdrBytes + (size_t)cap * sizeof(batch::JobDesc);
+    CK(cudaMallocHost((void **)&R.hstage, stage_bytes));
+    CK(cudaMalloc((void **)&R.dstage, stage_bytes));
+    CK(cudaMallocHost((void **)&R.hoff, ((size_t)cap + 1) * sizeof(uint64_t)));
+    CK(cudaMalloc((void **)&R.doff, ((size_t)cap + 1) * sizeof(uint64_t)));
+    CK(cudaMalloc((void **)&R.tables, (size_t)cap * batch::kTableBytes));
+    R.cap = cap;
     return EPSM_OK;
+}
+
+batch::BatchParams batch_params(epsm_ctx *c) {
+    BatchRes &R = c->batch;
+    batch::BatchParams p;
+    memset(&p, 0, sizeof(p));
+    p.hdr = reinterpret_cast<const batch::Header *>(R.dstage);
+    p.jobs = reinterpret_cast<const batch::JobDesc *>(R.dstage + kBatchHdrBytes);
+    p.tables = R.tables;
+    p.offsets = R.doff;
+    p.seg_count = c->seg_count;
+    p.seg_mask = c->seg_mask;
+    p.range_total = c->range_total;
+    p.err = &c->misc->err;
+    p.misc = c->misc;
+    return p;
+}
+
+constexpr int kTableGrid = 256;
+
+// The four steps of a batched submission, enqueued on s.
+cudaError_t enqueue_batch(epsm_ctx *c, const batch::BatchParams &p, size_t up, size_t down,
+                          cudaStream_t s) {
+    BatchRes &R = c->batch;
+    cudaError_t e = cudaMemcpyAsync(R.dstage, R.hstage, up, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    batch::build_tables_kernel<<<kTableGrid, 256, 0, s>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    void *args[] = {(void *)&p};
+    e = cudaLaunchCooperativeKernel((const void *)batch_stream_kernel, dim3(R.grid),
+                                    dim3(stream::kThreadsStream), args, sizeof(batch::BatchSmem), s);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(R.hoff, R.doff, down, cudaMemcpyDeviceToHost, s);
+}
+
+// Captures the submission into a graph sized for the full capacity; the two
+// copies' sizes are set per launch.  Any failure leaves direct launches in use.
+void build_batch_graph(epsm_ctx *c) {
+    BatchRes &R = c->batch;
+    if (R.exec) {
+        cudaGraphExecDestroy(R.exec);
+        R.exec = nullptr;
+    }
+    const batch::BatchParams p = batch_params(c);
+    const size_t up = kBatchHdrBytes + (size_t)R.cap * sizeof(batch::JobDesc);
+    const size_t down = ((size_t)R.cap + 1) * sizeof(uint64_t);
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        R.graph_failed = true;
+        return;
+    }
+    cudaError_t e = enqueue_batch(c, p, up, down, c->stream);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        R.graph_failed = true;
+        return;
+    }
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    R.up = R.down = nullptr;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        cudaGraphNodeGetType(nd, &t);
+        if (t != cudaGraphNodeTypeMemcpy) continue;
+        cudaMemcpy3DParms mp;
+        memset(&mp, 0, sizeof(mp));
+        cudaGraphMemcpyNodeGetParams(nd, &mp);
+        if (mp.kind == cudaMemcpyHostToDevice) R.up = nd; else R.down = nd;
+    }
+    if (!R.up || !R.down || cudaGraphInstantiate(&R.exec, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        R.exec = nullptr;
+        R.graph_failed = true;
+        return;
+    }
+    cudaGraphDestroy(g);
+    R.graph_seg_cap = c->seg_cap;
 }
 
 epsm_status batch_impl(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts,
@@ -328,58 +408,73 @@ epsm_status batch_impl(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts
                        uint64_t *positions, uint64_t capacity, uint64_t *offsets,
                        cudaStream_t s) {
     epsm_status st;
-    if ((st = grow_pinned(c, &c->hpairs, &c->dpairs, &c->pairs_cap, npairs)) != EPSM_OK) return st;
-    if ((st = grow_pinned(c, &c->hoffsets, &c->doffsets, &c->offsets_cap, npairs + 1)) != EPSM_OK)
-        return st;
-    uint64_t tile0 = 0;
-    std::vector<uint8_t> empty(npairs, 0);
+    if ((st = ensure_batch(c, npairs, s)) != EPSM_OK) return st;
+    BatchRes &R = c->batch;
+    if (R.grid == 0) R.grid = batch_grid(c->sms);
+    if (R.grid == 0) return EPSM_ERR_CUDA;
+    batch::Header &H = *reinterpret_cast<batch::Header *>(R.hstage);
+    batch::JobDesc *jobs = reinterpret_cast<batch::JobDesc *>(R.hstage + kBatchHdrBytes);
+    uint32_t nj = 0, nt = 0;
+    uint64_t stage0 = 0;
     for (uint32_t i = 0; i < npairs; ++i) {
-        BatchPair &bp = c->hpairs[i];
-        memset(&bp, 0, sizeof(bp));
-        int v = c->variant[ms[i]];
-        bp.job = make_job(texts[i], ns[i], pack_pattern(patterns[i], ms[i]));
-        bp.variant = (uint32_t)v;
-        bp.tile0 = tile0;
-        uint64_t nt = tiles_for(bp.job.delta, ns[i], ms[i], v);
-        empty[i] = nt == 0;
-        tile0 += nt;
+        const int v = c->variant[ms[i]];
+        const SearchJob J = make_job(texts[i], ns[i], pack_pattern(patterns[i], ms[i]));
+        const uint64_t nst = stages_for(J.delta, ns[i], ms[i], v);
+        if (nst == 0) continue;
+        batch::JobDesc &D = jobs[nj++];
+        memset(&D, 0, sizeof(D));
+        D.job = J;
+        D.stage0 = stage0;
+        D.nstages = nst;
+        D.chunk_full0 = (J.delta + 15u) / 16u;
+        D.chunk_full1 = J.lim / 16u;
+        D.variant = (uint32_t)v;
+        D.table = v == V_BLOCK8 ? nt++ : batch::kNoTable;
+        D.pair = i;
+        D.off = variant_offset(v);
+        stage0 += nst;
     }
-    const uint64_t ntiles = tile0;
+    memset(&H, 0, sizeof(H));
+    H.njobs = nj;
+    H.ntables = nt;
+    H.nstages = stage0;
+    H.range_stages = std::max<uint64_t>(1, (stage0 + R.grid - 1) / R.grid);
+    H.capacity = capacity;
+    H.positions = positions;
+    H.emit = capacity > 0 ? 1u : 0u;
+    if (nj == 0) {
+        for (uint32_t i = 0; i <= npairs; ++i) offsets[i] = 0;
+        return EPSM_OK;
+    }
+    if ((st = ensure_stream_scratch(c, stage0, s)) != EPSM_OK) return st;
     if ((st = order_after_previous(c, s)) != EPSM_OK) return st;
-    if (ntiles > 0) {
-        if ((st = ensure_status(c, ntiles, s)) != EPSM_OK) return st;
-        uint32_t tag = 0;
-        if ((st = next_tag(c, s, &tag)) != EPSM_OK) return st;
-        CK(cudaMemcpyAsync(c->dpairs, c->hpairs, sizeof(BatchPair) * npairs,
-                           cudaMemcpyHostToDevice, s));
-        BatchParams p;
-        memset(&p, 0, sizeof(p));
-        p.pairs = c->dpairs;
-        p.npairs = npairs;
-        p.ntiles = ntiles;
-        p.out.positions = positions;
-        p.out.capacity = capacity;
-        p.out.status = c->status;
-        p.out.err = &c->misc->err;
-        p.out.tag = tag;
-        p.offsets = c->doffsets;
-        p.misc = c->misc;
-        const void *fn = (const void *)batch_kernel<kDefaultU>;
-        uint64_t grid = std::min<uint64_t>(ntiles, (uint64_t)c->sms * blocks_per_sm(fn));
-        batch_kernel<kDefaultU><<<(unsigned)grid, kThreads, 0, s>>>(p);
-        CK(cudaGetLastError());
-        c->launches += 1;
-        CK(cudaMemcpyAsync(c->hoffsets, c->doffsets, sizeof(uint64_t) * (npairs + 1),
-                           cudaMemcpyDeviceToHost, s));
+    const size_t up = kBatchHdrBytes + (size_t)nj * sizeof(batch::JobDesc);
+    const size_t down = ((size_t)nj + 1) * sizeof(uint64_t);
+    if (!R.graph_failed && (!R.exec || R.graph_seg_cap != c->seg_cap)) build_batch_graph(c);
+    bool launched = false;
+    if (!R.graph_failed && R.exec) {
+        if (cudaGraphExecMemcpyNodeSetParams1D(R.exec, R.up, R.dstage, R.hstage, up,
+                                               cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaGraphExecMemcpyNodeSetParams1D(R.exec, R.down, R.hoff, R.doff, down,
+                                               cudaMemcpyDeviceToHost) == cudaSuccess &&
+            cudaGraphLaunch(R.exec, s) == cudaSuccess) {
+            launched = true;
+        } else {
+            cudaGetLastError();
+            R.graph_failed = true;
+        }
     }
+    if (!launched) CK(enqueue_batch(c, batch_params(c), up, down, s));
+    c->launches += 2;  // table build + batched scan
     if ((st = mark_done(c, s)) != EPSM_OK) return st;
     uint32_t err = 0;
-    if (ntiles > 0) {
-        if ((st = read_misc(c, s, &err)) != EPSM_OK) return st;
-    }
-    // Pairs without tiles (n < m) own an empty range at the next pair's offset.
-    offsets[npairs] = ntiles > 0 ? c->hoffsets[npairs] : 0;
-    for (uint32_t i = npairs; i-- > 0;) offsets[i] = empty[i] ? offsets[i + 1] : c->hoffsets[i];
+    if ((st = read_misc(c, s, &err)) != EPSM_OK) return st;
+    // job offsets -> pair offsets; pairs without stages (n < m) own an empty
+    // range at the next pair's offset
+    std::vector<uint64_t> by_pair(npairs, ~0ull);
+    for (uint32_t j = 0; j < nj; ++j) by_pair[jobs[j].pair] = R.hoff[j];
+    offsets[npairs] = R.hoff[nj];
+    for (uint32_t i = npairs; i-- > 0;) offsets[i] = by_pair[i] != ~0ull ? by_pair[i] : offsets[i + 1];
     if (err & kErrTimeout) return EPSM_ERR_TIMEOUT;
     return offsets[npairs] > capacity ? EPSM_ERR_CAPACITY : EPSM_OK;
 }
@@ -425,13 +520,9 @@ EPSM_API epsm_status epsm_destroy(epsm_ctx *c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     cudaDeviceSynchronize();
-    if (c->status) cudaFree(c->status);
     if (c->misc) cudaFree(c->misc);
     if (c->hmisc) cudaFreeHost(c->hmisc);
-    if (c->hpairs) cudaFreeHost(c->hpairs);
-    if (c->dpairs) cudaFree(c->dpairs);
-    if (c->hoffsets) cudaFreeHost(c->hoffsets);
-    if (c->doffsets) cudaFree(c->doffsets);
+    free_batch(c->batch);
     if (c->seg_count) cudaFree(c->seg_count);
     if (c->range_total) cudaFree(c->range_total);
     if (c->seg_mask) cudaFree(c->seg_mask);
@@ -579,6 +670,10 @@ EPSM_API epsm_status epsm_set_variant(epsm_ctx *c, uint32_t m, int variant) {
 }
 
 EPSM_API uint64_t epsm_launch_count(epsm_ctx *c) { return c ? c->launches : 0; }
+
+EPSM_API int epsm_batch_uses_graph(epsm_ctx *c) {
+    return c && c->batch.exec != nullptr && !c->batch.graph_failed ? 1 : 0;
+}
 
 // ---------------------------------------------------------------------------
 // Search without any allocation (epsm_search_static).

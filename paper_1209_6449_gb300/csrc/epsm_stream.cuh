@@ -148,11 +148,12 @@ struct StreamParams {
     int emit;              // 0: count only
 };
 
-__device__ __forceinline__ uint4 staged_chunk(const StreamParams &P, const uint8_t *buf,
-                                              uint64_t c0, uint64_t c) {
-    if (c >= P.chunk_full0 && c < P.chunk_full1)
-        return *reinterpret_cast<const uint4 *>(buf + (c - c0) * 16u);
-    return load_chunk(P.job, c);
+// Chunk c of job J as staged in `buf` (the stage's first chunk is c0), or read
+// from global memory when it is not fully inside the text (ragged ends).
+__device__ __forceinline__ uint4 staged_chunk(const SearchJob &J, uint64_t cf0, uint64_t cf1,
+                                              const uint8_t *buf, uint64_t c0, uint64_t c) {
+    if (c >= cf0 && c < cf1) return *reinterpret_cast<const uint4 *>(buf + (c - c0) * 16u);
+    return load_chunk(J, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -214,75 +215,94 @@ __device__ __forceinline__ void producer(const StreamParams &P, StreamSmem &S) {
 
 // A chunk read through the ragged-end path (its stage is not entirely inside
 // the text): out of line, to keep the hot loop small.
-__device__ __noinline__ uint4 edge_chunk(const StreamParams &P, const uint8_t *buf, uint64_t c0,
-                                         uint64_t c) {
-    return staged_chunk(P, buf, c0, c);
+__device__ __noinline__ uint4 edge_chunk(const SearchJob &J, uint64_t cf0, uint64_t cf1,
+                                         const uint8_t *buf, uint64_t c0, uint64_t c) {
+    return staged_chunk(J, cf0, cf1, buf, c0, c);
+}
+
+// Filter and verify one consumer warp's segment of a staged stage of job J:
+// the stage holds the job's chunks c0 .. c0+1024 (+ halo); lane l takes chunks
+// 32u + l of segment w.  Writes the four 16-bit hit masks to h and returns the
+// lane's hit count.
+template <int V, int MP>
+__device__ __forceinline__ uint32_t stage_hits(const SearchJob &J, uint64_t cf0, uint64_t cf1,
+                                               const BcastWords &B, const uint8_t *table,
+                                               const uint32_t *pblk, const uint8_t *buf,
+                                               uint64_t c0, int w, int lane, uint32_t (&h)[4]) {
+    constexpr int OFF = (V == V_BLOCK8) ? -7 : 0;
+    const uint32_t lane_off = (uint32_t)(w * kSegChunks + lane) * 16u;  // byte offset in a stage
+    // stage entirely inside the text (all but the first and last stages):
+    // 32-bit shared-memory offsets, no per-chunk bounds checks
+    const bool inside = c0 >= cf0 && c0 + kStageChunks + 1u <= cf1;
+    uint4 ch[4];
+    uint4 halo = make_uint4(0u, 0u, 0u, 0u);
+    if (inside) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            ch[u] = *reinterpret_cast<const uint4 *>(buf + lane_off + 512u * u);
+        if (V != V_BLOCK8 && lane == 0) halo = *reinterpret_cast<const uint4 *>(buf + lane_off + 2048u);
+    } else {
+        const uint64_t cw = c0 + (uint64_t)w * kSegChunks;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ch[u] = edge_chunk(J, cf0, cf1, buf, c0, cw + 32u * u + lane);
+        if (V != V_BLOCK8 && lane == 0) halo = edge_chunk(J, cf0, cf1, buf, c0, cw + kSegChunks);
+    }
+    const int64_t sp0 = (int64_t)((c0 + (uint64_t)w * kSegChunks) * 16u) + OFF;
+    const bool interior = sp0 >= (int64_t)J.delta && sp0 + (int64_t)(kSegChunks * 16) - 1 <= J.pmax;
+    uint32_t cnt = 0u;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const uint4 cur = ch[u];
+        const uint4 nsrc = (lane == 0) ? (u + 1 < 4 ? ch[u + 1 < 4 ? u + 1 : u] : halo) : cur;
+        const int64_t p0 = sp0 + (int64_t)((32 * u + lane) * 16);
+        uint32_t hh = chunk_hits<V, MP>(J, cur, nsrc, p0, B, table, pblk, lane);
+        if (!interior) hh &= range_mask((int64_t)J.delta - p0, J.pmax - p0);
+        h[u] = hh;
+        cnt += __popc(hh);
+    }
+    return cnt;
+}
+
+// Per-segment results of phase 1: the count always, the lane-major packed
+// masks (lane l's four chunk masks as one 8-byte word) only if it has hits.
+__device__ __forceinline__ void store_segment(uint32_t *seg_count, uint16_t *seg_mask,
+                                              unsigned long long *range_total,
+                                              uint64_t range_stages, uint64_t st, uint64_t seg,
+                                              uint32_t cnt, const uint32_t (&h)[4], bool emit,
+                                              int lane) {
+    const uint32_t wc = __any_sync(kFull, cnt != 0u) ? warp_sum(cnt) : 0u;
+    if (lane == 0) {
+        seg_count[seg] = wc;
+        if (wc) atomicAdd(&range_total[st / range_stages], (unsigned long long)wc);
+    }
+    if (wc != 0u && emit) {
+        uint2 packed;
+        packed.x = (h[0] & 0xFFFFu) | (h[1] << 16);
+        packed.y = (h[2] & 0xFFFFu) | (h[3] << 16);
+        reinterpret_cast<uint2 *>(seg_mask + seg * kSegChunks)[lane] = packed;
+    }
 }
 
 template <int V, int MP>
 __device__ __forceinline__ void filter_stages(const StreamParams &P, StreamSmem &S, int w, int lane,
                                               bool *ok) {
-    constexpr int OFF = (V == V_BLOCK8) ? -7 : 0;
     const SearchJob &J = P.job;
     const BcastWords B(J.pat);
-    const uint32_t lane_off = (uint32_t)(w * kSegChunks + lane) * 16u;  // byte offset in a stage
     int s = 0;
     uint32_t phase = 0;
     for (;;) {
         if (!warp_wait(&S.full[s], phase)) { *ok = false; break; }
         const uint64_t st = S.stage_id[s];
         if (st == kEndStage) break;
-        const uint64_t c0 = st * kStageChunks;
-        const uint8_t *buf = S.buf[s];
-        // stage entirely inside the text (all but the first and last stages):
-        // 32-bit shared-memory offsets, no per-chunk bounds checks
-        const bool inside = c0 >= P.chunk_full0 && c0 + kStageChunks + 1u <= P.chunk_full1;
-        uint4 ch[4];
-        uint4 halo = make_uint4(0u, 0u, 0u, 0u);
-        if (inside) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                ch[u] = *reinterpret_cast<const uint4 *>(buf + lane_off + 512u * u);
-            if (V != V_BLOCK8 && lane == 0)
-                halo = *reinterpret_cast<const uint4 *>(buf + lane_off + 2048u);
-        } else {
-            const uint64_t cw = c0 + (uint64_t)w * kSegChunks;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) ch[u] = edge_chunk(P, buf, c0, cw + 32u * u + lane);
-            if (V != V_BLOCK8 && lane == 0) halo = edge_chunk(P, buf, c0, cw + kSegChunks);
-        }
-        const int64_t sp0 = (int64_t)((c0 + (uint64_t)w * kSegChunks) * 16u) + OFF;
-        const bool interior = sp0 >= (int64_t)J.delta &&
-                              sp0 + (int64_t)(kSegChunks * 16) - 1 <= J.pmax;
         uint32_t h[4];
-        uint32_t cnt = 0u;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint4 cur = ch[u];
-            const uint4 nsrc = (lane == 0) ? (u + 1 < 4 ? ch[u + 1 < 4 ? u + 1 : u] : halo) : cur;
-            const int64_t p0 = sp0 + (int64_t)((32 * u + lane) * 16);
-            uint32_t hh = chunk_hits<V, MP>(J, cur, nsrc, p0, B, S.table, S.pblk, lane);
-            if (!interior) hh &= range_mask((int64_t)J.delta - p0, J.pmax - p0);
-            h[u] = hh;
-            cnt += __popc(hh);
-        }
+        const uint32_t cnt = stage_hits<V, MP>(J, P.chunk_full0, P.chunk_full1, B, S.table, S.pblk,
+                                               S.buf[s], st * kStageChunks, w, lane, h);
         // the stage buffer is no longer needed: release it to the producer
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[s]);
         if (++s == kStages) { s = 0; phase ^= 1u; }
-        const uint32_t wc = __any_sync(kFull, cnt != 0u) ? warp_sum(cnt) : 0u;
-        const uint64_t seg = st * kConsumerWarps + (uint64_t)w;
-        if (lane == 0) {
-            P.seg_count[seg] = wc;
-            if (wc) atomicAdd(&P.range_total[st / P.range_stages], (unsigned long long)wc);
-        }
-        if (wc != 0u && P.emit) {
-            // lane-major: lane l's four chunk masks are one 8-byte word
-            uint2 packed;
-            packed.x = (h[0] & 0xFFFFu) | (h[1] << 16);
-            packed.y = (h[2] & 0xFFFFu) | (h[3] << 16);
-            reinterpret_cast<uint2 *>(P.seg_mask + seg * kSegChunks)[lane] = packed;
-        }
+        store_segment(P.seg_count, P.seg_mask, P.range_total, P.range_stages, st,
+                      st * kConsumerWarps + (uint64_t)w, cnt, h, P.emit != 0, lane);
     }
 }
 
@@ -292,10 +312,10 @@ __device__ __forceinline__ void filter_stages(const StreamParams &P, StreamSmem 
 // staged in shared memory as offsets inside the segment, in output order, and
 // written as consecutive 8-byte positions — in one pass when they fit in the
 // 512-entry stage (the common case), else one pass per step.
-template <int OFF>
-__device__ __forceinline__ void emit_segment(const StreamParams &P, uint64_t seg, uint64_t idx0,
-                                             uint2 packed, uint16_t *stage, int lane) {
-    const SearchJob &J = P.job;
+//   s0: the start (user coordinates) of bit 0 of the segment's first chunk.
+__device__ __forceinline__ void emit_segment(uint64_t *positions, uint64_t capacity, uint32_t *err,
+                                             int64_t s0, uint64_t idx0, uint2 packed,
+                                             uint16_t *stage, int lane) {
     uint32_t h[4], c[4], inc[4], T[4];
     h[0] = packed.x & 0xFFFFu;
     h[1] = packed.x >> 16;
@@ -317,8 +337,7 @@ __device__ __forceinline__ void emit_segment(const StreamParams &P, uint64_t seg
 #pragma unroll
     for (int u = 0; u < 4; ++u) T[u] = __shfl_sync(kFull, inc[u], 31);
     const uint32_t total = T[0] + T[1] + T[2] + T[3];
-    const int64_t s0 = (int64_t)(seg * kSegChunks * 16u) + OFF - (int64_t)J.delta;
-    if (lane == 0 && idx0 + total > P.capacity) atomicOr(P.err, kErrCapacity);
+    if (lane == 0 && idx0 + total > capacity) atomicOr(err, kErrCapacity);
     if (total <= 32u * 16u) {
         uint32_t before = 0u;
 #pragma unroll
@@ -335,7 +354,7 @@ __device__ __forceinline__ void emit_segment(const StreamParams &P, uint64_t seg
         __syncwarp();
         for (uint32_t q = lane; q < total; q += 32u) {
             const uint64_t idx = idx0 + q;
-            if (idx < P.capacity) P.positions[idx] = (uint64_t)(s0 + stage[q]);
+            if (idx < capacity) positions[idx] = (uint64_t)(s0 + stage[q]);
         }
         __syncwarp();
         return;
@@ -353,15 +372,15 @@ __device__ __forceinline__ void emit_segment(const StreamParams &P, uint64_t seg
         __syncwarp();
         for (uint32_t q = lane; q < T[u]; q += 32u) {
             const uint64_t idx = idx0 + run + q;
-            if (idx < P.capacity) P.positions[idx] = (uint64_t)(s0 + stage[q]);
+            if (idx < capacity) positions[idx] = (uint64_t)(s0 + stage[q]);
         }
         __syncwarp();
         run += T[u];
     }
 }
 
-__device__ __forceinline__ uint2 load_masks(const StreamParams &P, uint64_t seg, int lane) {
-    return reinterpret_cast<const uint2 *>(P.seg_mask + seg * kSegChunks)[lane];
+__device__ __forceinline__ uint2 load_masks(const uint16_t *seg_mask, uint64_t seg, int lane) {
+    return reinterpret_cast<const uint2 *>(seg_mask + seg * kSegChunks)[lane];
 }
 
 // Phase 3 for the consumer warps: block-ordered prefix of the segment counts
@@ -394,7 +413,7 @@ __device__ __forceinline__ void emit_block(const StreamParams &P, StreamSmem &S,
             int j = __ffs(todo) - 1;
             todo &= todo - 1u;
             uint64_t sj = sb + (uint64_t)w * 32u + (uint64_t)j;
-            uint2 cur = load_masks(P, sj, lane);
+            uint2 cur = load_masks(P.seg_mask, sj, lane);
             for (;;) {
                 const uint64_t ej = __shfl_sync(kFull, excl, j);
                 int jn = -1;
@@ -404,9 +423,11 @@ __device__ __forceinline__ void emit_block(const StreamParams &P, StreamSmem &S,
                     jn = __ffs(todo) - 1;
                     todo &= todo - 1u;
                     sn = sb + (uint64_t)w * 32u + (uint64_t)jn;
-                    nxt = load_masks(P, sn, lane);
+                    nxt = load_masks(P.seg_mask, sn, lane);
                 }
-                emit_segment<OFF>(P, sj, ej, cur, S.emit_stage[w], lane);
+                const int64_t s0 =
+                    (int64_t)(sj * kSegChunks * 16u) + OFF - (int64_t)P.job.delta;
+                emit_segment(P.positions, P.capacity, P.err, s0, ej, cur, S.emit_stage[w], lane);
                 if (jn < 0) break;
                 j = jn;
                 sj = sn;

@@ -106,3 +106,15 @@ def test_search_host_matches_oracle(ctx):
     assert offs[-1] == total
     for k, w in enumerate(want):
         assert np.array_equal(pos[offs[k]:offs[k + 1]], w), k
+
+
+def test_batch_graph_replay_and_reuse(ctx, torch):
+    """Repeated batches of different sizes reuse the captured submission and
+    stay exact."""
+    for seed, npairs in ((11, 40), (12, 7), (13, 64), (14, 1)):
+        pairs, hosts = _pairs(npairs, seed=seed, hi_log2=15)
+        pats = [p.pattern for p in pairs]
+        offs, out, want, _ = _run_batch(ctx, torch, hosts, pats)
+        for i, w in enumerate(want):
+            assert np.array_equal(out[offs[i]:offs[i + 1]], w), (seed, i)
+    print("batch graph replay:", ctx.batch_uses_graph)
