@@ -83,6 +83,7 @@ struct BatchRes {
     uint64_t *doff = nullptr;
     uint8_t *tables = nullptr;
     uint32_t cap = 0;           // jobs
+    cudaGraph_t graph = nullptr;     // kept: its node handles address the exec's copies
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t up = nullptr, down = nullptr;
     uint64_t graph_seg_cap = 0;      // scratch size the graph was built with
@@ -280,6 +281,7 @@ epsm_status read_misc(epsm_ctx *c, cudaStream_t s, uint32_t *err) {
 
 void free_batch(BatchRes &R) {
     if (R.exec) cudaGraphExecDestroy(R.exec);
+    if (R.graph) cudaGraphDestroy(R.graph);
     if (R.hstage) cudaFreeHost(R.hstage);
     if (R.dstage) cudaFree(R.dstage);
     if (R.hoff) cudaFreeHost(R.hoff);
@@ -354,52 +356,82 @@ cudaError_t enqueue_batch(epsm_ctx *c, const batch::BatchParams &p, size_t up, s
     return cudaMemcpyAsync(R.hoff, R.doff, down, cudaMemcpyDeviceToHost, s);
 }
 
-// Captures the submission into a graph sized for the full capacity; the two
-// copies' sizes are set per launch.  Any failure leaves direct launches in use.
+// Builds the submission as an explicit graph sized for the full capacity
+// (upload -> table build -> cooperative batched scan -> offsets download);
+// the two copies' sizes are set per launch.  Any failure leaves direct
+// launches in use (the reason is kept in the context's error string).
 void build_batch_graph(epsm_ctx *c) {
     BatchRes &R = c->batch;
     if (R.exec) {
         cudaGraphExecDestroy(R.exec);
         R.exec = nullptr;
     }
-    const batch::BatchParams p = batch_params(c);
+    if (R.graph) {
+        cudaGraphDestroy(R.graph);
+        R.graph = nullptr;
+    }
+    const batch::BatchParams p = batch_params(c);  // node arguments are copied when added
     const size_t up = kBatchHdrBytes + (size_t)R.cap * sizeof(batch::JobDesc);
     const size_t down = ((size_t)R.cap + 1) * sizeof(uint64_t);
     cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        R.graph_failed = true;
-        return;
+    cudaGraphNode_t n_up = nullptr, n_tab = nullptr, n_scan = nullptr, n_down = nullptr;
+    const char *what = "cudaGraphCreate";
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e == cudaSuccess) {
+        what = "memcpy node (upload)";
+        e = cudaGraphAddMemcpyNode1D(&n_up, g, nullptr, 0, R.dstage, R.hstage, up,
+                                     cudaMemcpyHostToDevice);
     }
-    cudaError_t e = enqueue_batch(c, p, up, down, c->stream);
-    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
-    if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+    if (e == cudaSuccess) {
+        what = "kernel node (tables)";
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof(kp));
+        void *args[] = {(void *)&p};
+        kp.func = (void *)batch::build_tables_kernel;
+        kp.gridDim = dim3(kTableGrid);
+        kp.blockDim = dim3(256);
+        kp.kernelParams = args;
+        e = cudaGraphAddKernelNode(&n_tab, g, &n_up, 1, &kp);
+    }
+    if (e == cudaSuccess) {
+        what = "kernel node (scan)";
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof(kp));
+        void *args[] = {(void *)&p};
+        kp.func = (void *)batch_stream_kernel;
+        kp.gridDim = dim3(R.grid);
+        kp.blockDim = dim3(stream::kThreadsStream);
+        kp.sharedMemBytes = sizeof(batch::BatchSmem);
+        kp.kernelParams = args;
+        e = cudaGraphAddKernelNode(&n_scan, g, &n_tab, 1, &kp);
+        if (e == cudaSuccess) {
+            what = "cooperative attribute";
+            cudaLaunchAttributeValue v;
+            memset(&v, 0, sizeof(v));
+            v.cooperative = 1;
+            e = cudaGraphKernelNodeSetAttribute(n_scan, cudaLaunchAttributeCooperative, &v);
+        }
+    }
+    if (e == cudaSuccess) {
+        what = "memcpy node (download)";
+        e = cudaGraphAddMemcpyNode1D(&n_down, g, &n_scan, 1, R.hoff, R.doff, down,
+                                     cudaMemcpyDeviceToHost);
+    }
+    if (e == cudaSuccess) {
+        what = "cudaGraphInstantiate";
+        e = cudaGraphInstantiate(&R.exec, g, 0);
+    }
+    if (e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
-        cudaGetLastError();
-        R.graph_failed = true;
-        return;
-    }
-    size_t nn = 0;
-    cudaGraphGetNodes(g, nullptr, &nn);
-    std::vector<cudaGraphNode_t> nodes(nn);
-    cudaGraphGetNodes(g, nodes.data(), &nn);
-    R.up = R.down = nullptr;
-    for (cudaGraphNode_t nd : nodes) {
-        cudaGraphNodeType t;
-        cudaGraphNodeGetType(nd, &t);
-        if (t != cudaGraphNodeTypeMemcpy) continue;
-        cudaMemcpy3DParms mp;
-        memset(&mp, 0, sizeof(mp));
-        cudaGraphMemcpyNodeGetParams(nd, &mp);
-        if (mp.kind == cudaMemcpyHostToDevice) R.up = nd; else R.down = nd;
-    }
-    if (!R.up || !R.down || cudaGraphInstantiate(&R.exec, g, 0) != cudaSuccess) {
-        cudaGraphDestroy(g);
+        snprintf(c->errbuf, sizeof(c->errbuf), "batch graph: %s: %s", what, cudaGetErrorString(e));
         cudaGetLastError();
         R.exec = nullptr;
         R.graph_failed = true;
         return;
     }
-    cudaGraphDestroy(g);
+    R.graph = g;
+    R.up = n_up;
+    R.down = n_down;
     R.graph_seg_cap = c->seg_cap;
 }
 

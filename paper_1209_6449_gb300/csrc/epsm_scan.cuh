@@ -4,9 +4,7 @@
 // The text is processed in tiles; each warp streams 16-byte chunks with
 // coalesced vector loads, a per-variant filter marks candidate starts (the
 // Section 3 procedures re-thought for 32-bit lanes), candidates are verified,
-// and the hits of a tile are compacted in order: warp ballot/popc and block
-// prefix sums inside the tile, a decoupled look-back across tiles for the
-// tile's global output offset.
+// and the hits are compacted in order (see epsm_stream.cuh).
 //
 // Coordinates.  `base` is the text pointer rounded down to 16 bytes and
 // `delta` = text - base.  An internal position P addresses base[P]; the user
@@ -38,34 +36,6 @@ constexpr int kHashSlots = 1 << kHashBits;
 // Error bits of the device error word.
 constexpr uint32_t kErrTimeout = 1u;   // a look-back wait gave up
 constexpr uint32_t kErrCapacity = 2u;  // an occurrence did not fit in the output
-
-// Tile status word: [63:42] call tag, [41:40] flag, [39:0] value.
-constexpr int kTagShift = 42;
-constexpr int kFlagShift = 40;
-constexpr uint64_t kValMask = (1ull << 40) - 1;
-constexpr uint32_t kFlagAgg = 1;
-constexpr uint32_t kFlagPre = 2;
-constexpr uint64_t kLookbackTimeoutNs = 2000000000ull;  // 2 s per wait
-
-// Look-back tuning.  Status words are spread kStatusStride words apart so that
-// the words of recent tiles, which every block polls, fall on different L2
-// lines instead of all on a few (a hot spot that serialised the polls).
-#ifndef EPSM_LB_K
-#define EPSM_LB_K 1
-#endif
-#ifndef EPSM_LB_STRIDE
-#define EPSM_LB_STRIDE 16
-#endif
-#ifndef EPSM_LB_HELP
-#define EPSM_LB_HELP 0
-#endif
-#ifndef EPSM_LB_SLEEP
-#define EPSM_LB_SLEEP 128
-#endif
-constexpr int kLookbackK = EPSM_LB_K;          // status words per lane per round
-constexpr int kStatusStride = EPSM_LB_STRIDE;  // uint64 words between tiles' status
-constexpr bool kLookbackHelp = EPSM_LB_HELP != 0;
-constexpr int kLookbackSleepNs = EPSM_LB_SLEEP;
 
 struct Pattern {
     uint32_t w[8];  // p packed little-endian, zero padded (the paper's blocks P_i, Section 2)
@@ -222,124 +192,6 @@ __device__ __forceinline__ uint64_t warp_sum64(uint64_t v) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
     return v;
-}
-
-// ---------------------------------------------------------------------------
-// decoupled look-back across tiles (called by one full warp)
-// ---------------------------------------------------------------------------
-
-__device__ __forceinline__ uint64_t pack_status(uint32_t tag, uint32_t flag, uint64_t v) {
-    return ((uint64_t)tag << kTagShift) | ((uint64_t)flag << kFlagShift) | (v & kValMask);
-}
-
-// Publishes the tile aggregate, walks back over its predecessors 32*K at a
-// time (K consecutive status words per lane) until one holds an inclusive
-// prefix, publishes this tile's inclusive prefix, and returns the exclusive
-// prefix (in every lane).  An inclusive prefix thus travels 32*K tiles per
-// round trip to L2; with 32 tiles per round trip the prefix chain, not HBM,
-// bounded the scan.  Each wait is bounded in time; on expiry the error word
-// gets kErrTimeout and the wait is abandoned (missing values count as 0), so
-// the kernel always terminates.
-template <int K = kLookbackK>
-__device__ uint64_t tile_lookback(uint64_t *status, uint64_t tile, uint64_t agg, uint32_t tag,
-                                  uint32_t *err, int lane) {
-    if (tile == 0) {
-        if (lane == 0) st_relaxed_u64(status, pack_status(tag, kFlagPre, agg));
-        return 0;
-    }
-    if (lane == 0) st_relaxed_u64(status + tile * kStatusStride, pack_status(tag, kFlagAgg, agg));
-    uint64_t excl = 0;
-    int64_t end = (int64_t)tile;  // window: tiles end-1 down to end-32K
-    uint64_t t0 = 0;
-    bool timed_out = false;
-    while (true) {
-        uint64_t v[K];
-        uint32_t f[K];
-        int fl, lp;
-        while (true) {
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const int64_t idx = end - 1 - (int64_t)(lane * K + j);
-                if (idx >= 0) {
-                    const uint64_t s = ld_relaxed_u64(status + idx * kStatusStride);
-                    f[j] = ((uint32_t)(s >> kTagShift) == tag) ? (uint32_t)(s >> kFlagShift) & 3u : 0u;
-                    v[j] = s & kValMask;
-                } else {
-                    f[j] = kFlagPre;  // before tile 0: an empty prefix
-                    v[j] = 0;
-                }
-            }
-            lp = K;
-#pragma unroll
-            for (int j = K - 1; j >= 0; --j)
-                if (f[j] == kFlagPre) lp = j;
-            const uint32_t pb = __ballot_sync(kFull, lp < K);
-            fl = pb ? __ffs(pb) - 1 : 32;
-            // tiles up to the nearest inclusive prefix must have published
-            bool ready = true;
-#pragma unroll
-            for (int j = 0; j < K; ++j)
-                if (lane < fl || (lane == fl && j <= lp)) ready &= f[j] != 0u;
-            if (__all_sync(kFull, ready)) break;
-            if (timed_out) {
-#pragma unroll
-                for (int j = 0; j < K; ++j)
-                    if (f[j] == 0u) { f[j] = kFlagPre; v[j] = 0; }
-                lp = K;
-#pragma unroll
-                for (int j = K - 1; j >= 0; --j)
-                    if (f[j] == kFlagPre) lp = j;
-                const uint32_t pb2 = __ballot_sync(kFull, lp < K);
-                fl = pb2 ? __ffs(pb2) - 1 : 32;
-                break;
-            }
-            const uint64_t now = globaltimer_ns();
-            if (t0 == 0) t0 = now;
-            if (__any_sync(kFull, now - t0 > kLookbackTimeoutNs)) {
-                timed_out = true;
-                if (lane == 0) atomicOr(err, kErrTimeout);
-            }
-            __nanosleep(kLookbackSleepNs);
-        }
-        uint64_t mine = 0;
-#pragma unroll
-        for (int j = 0; j < K; ++j)
-            if (lane < fl || (lane == fl && j <= lp)) mine += v[j];
-        const uint64_t wsum = warp_sum64(mine);
-        if (kLookbackHelp && fl < 32 && end == (int64_t)tile && !timed_out) {
-            // Help the prefix chain: every predecessor between the inclusive
-            // prefix found and this tile gets its own inclusive prefix,
-            // excl_total - (sum of the aggregates after it), so later tiles
-            // find one close by instead of waiting for each owner in turn.
-            const uint64_t total = excl + wsum;  // exclusive prefix of `tile`
-            uint64_t lane_sum = 0;
-#pragma unroll
-            for (int j = 0; j < K; ++j)
-                if (lane < fl || (lane == fl && j <= lp)) lane_sum += v[j];
-            uint64_t before = lane_sum;  // inclusive scan over lanes of lane_sum
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint64_t t = __shfl_up_sync(kFull, before, d);
-                if (lane >= d) before += t;
-            }
-            before -= lane_sum;  // sum of the aggregates of tiles closer to `tile`
-#pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const bool in = lane < fl || (lane == fl && j < lp);
-                if (in && f[j] == kFlagAgg) {
-                    const int64_t idx = end - 1 - (int64_t)(lane * K + j);
-                    st_relaxed_u64(status + idx * kStatusStride,
-                                   pack_status(tag, kFlagPre, total - before));
-                }
-                if (lane < fl || (lane == fl && j <= lp)) before += v[j];
-            }
-        }
-        excl += wsum;
-        if (fl < 32) break;
-        end -= 32 * K;
-    }
-    if (lane == 0) st_relaxed_u64(status + tile * kStatusStride, pack_status(tag, kFlagPre, excl + agg));
-    return excl;
 }
 
 }  // namespace epsm

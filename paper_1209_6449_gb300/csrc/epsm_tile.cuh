@@ -1,41 +1,16 @@
-// Per-tile scan: filter, verify, in-tile compaction, look-back, ordered emit.
+// Per-chunk filters and verify of the three length regimes (Section 3).
 //
-// Tile layout.  A tile is kThreads*U consecutive 16-byte chunks.  Warp w owns
-// the 32*U chunks starting at tile_chunk0 + 32*U*w; at step u lane l holds chunk
-// 32*u + l of that run (every load instruction of the warp covers 512
-// contiguous bytes).  The bytes a window needs beyond its own chunk come from
-// the next lane's registers (one shuffle per word); lane 31 takes them from
-// lane 0's chunk of step u+1, and at the last step from a halo chunk that lane
-// 0 loads after the warp's run.
-//
-// Hit masks.  For each chunk a 16-bit mask marks hits: bit i <-> internal
-// start pos0 + OFF + i, with pos0 = 16*chunk.  OFF = 0 for the window variants;
-// the block variant reports candidate s = 8b - j from block b, j in [0, 8), so
-// a chunk's two blocks cover starts [pos0 - 7, pos0 + 8] and OFF = -7.  Masks
-// are in ascending position order across (warp, step, lane, bit), which is
-// the order positions are written in.
+// A chunk is 16 text bytes held as four little-endian 32-bit words; a lane
+// also sees the next chunk (its neighbour lane's, by a shuffle).  For each
+// chunk a 16-bit mask marks hits: bit i <-> internal start pos0 + OFF + i,
+// with pos0 = 16*chunk.  OFF = 0 for the window variants; the block variant
+// reports candidate s = 8b - j from block b, j in [0, 8), so a chunk's two
+// blocks cover starts [pos0 - 7, pos0 + 8] and OFF = -7.
 #pragma once
 
 #include "epsm_scan.cuh"
 
 namespace epsm {
-
-struct TileSmem {
-    uint32_t next_tile;
-    uint32_t tile_total;
-    uint64_t tile_off;
-    uint32_t warp_off[kWarps];
-    uint32_t pblk[16];              // block variant: p[j..j+7] as (lo, hi), j = 0..7
-    uint8_t table[kHashSlots];      // block variant: fingerprint slots (Section 3.4, table L)
-};
-
-struct TileOut {
-    uint64_t *positions;  // device, ascending output (global index space)
-    uint64_t capacity;    // entries available in positions
-    uint64_t *status;     // look-back status words, indexed by global tile
-    uint32_t *err;        // device error word
-    uint32_t tag;         // call tag for status words
-};
 
 // Pattern preprocessing for the block variant (Section 3.4, table L): the
 // fingerprints of the eight pattern blocks p[j..j+7], j = 0..7.  Must be
@@ -227,90 +202,6 @@ __device__ __forceinline__ uint32_t chunk_hits(const SearchJob &J, const uint4 c
         const uint32_t t1 = table[h1];
         if (t0 | t1) return block_candidates(J, cur, p0, pblk, t0, t1);
         return 0u;
-    }
-}
-
-// Scan one tile of job J.  `gtile` indexes the look-back status words,
-// `ltile` is the tile's index inside the job.  Returns nothing; writes the
-// tile's positions at out_base + (exclusive prefix of gtile).
-//   count_out: if non-null, receives exclusive+total (the job total when this
-//   is the job's last tile); first_out: if non-null, receives the exclusive
-//   prefix (the job's output offset when this is the job's first tile).
-template <int V, int U, int MP>
-__device__ __forceinline__ void scan_tile(const SearchJob &J, uint64_t ltile, uint64_t gtile,
-                                          const BcastWords &B, TileSmem &sm, const TileOut &O,
-                                          uint64_t *count_out, uint64_t *first_out,
-                                          int64_t pos_bias) {
-    constexpr int OFF = (V == V_BLOCK8) ? -7 : 0;
-    constexpr uint64_t kTileChunks = (uint64_t)kThreads * U;
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const uint64_t c0 = ltile * kTileChunks + (uint64_t)warp * 32u * U;
-
-    uint4 ch[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) ch[u] = load_chunk(J, c0 + 32u * u + lane);
-    uint4 halo = make_uint4(0u, 0u, 0u, 0u);
-    if (V != V_BLOCK8 && lane == 0) halo = load_chunk(J, c0 + 32u * U);
-
-    const int64_t tp0 = (int64_t)(ltile * kTileChunks * 16u) + OFF;
-    const bool interior = tp0 >= (int64_t)J.delta &&
-                          tp0 + (int64_t)(kTileChunks * 16u) - 1 <= J.pmax;
-
-    uint32_t hit[U];
-    uint32_t cnt = 0u;
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const uint4 cur = ch[u];
-        const uint4 nsrc = (lane == 0) ? (u + 1 < U ? ch[u + 1 < U ? u + 1 : u] : halo) : cur;
-        const int64_t p0 = (int64_t)((c0 + 32u * u + lane) * 16u) + OFF;
-        uint32_t h = chunk_hits<V, MP>(J, cur, nsrc, p0, B, sm.table, sm.pblk, lane);
-        if (!interior) h &= range_mask((int64_t)J.delta - p0, J.pmax - p0);
-        hit[u] = h;
-        cnt += __popc(h);
-    }
-
-    // in-tile prefix sums: warp totals -> block scan (warp 0) -> look-back
-    const uint32_t wt = warp_sum(cnt);
-    if (lane == 0) sm.warp_off[warp] = wt;
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t v = lane < kWarps ? sm.warp_off[lane] : 0u;
-        const uint32_t inc = warp_incl_scan(v, lane);
-        const uint32_t total = __shfl_sync(kFull, inc, 31);
-        if (lane < kWarps) sm.warp_off[lane] = inc - v;
-        const uint64_t excl = tile_lookback(O.status, gtile, total, O.tag, O.err, lane);
-        if (lane == 0) {
-            sm.tile_off = excl;
-            sm.tile_total = total;
-            if (count_out) *count_out = excl + total;
-            if (first_out) *first_out = excl;
-        }
-    }
-    __syncthreads();
-
-    if (sm.tile_total != 0u && O.capacity != 0ull) {
-        uint64_t base = sm.tile_off + sm.warp_off[warp];
-        uint32_t run = 0u;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint32_t c = __popc(hit[u]);
-            if (__any_sync(kFull, c != 0u)) {
-                const uint32_t inc = warp_incl_scan(c, lane);
-                uint64_t idx = base + run + inc - c;
-                const int64_t s0 = (int64_t)((c0 + 32u * u + lane) * 16u) + OFF -
-                                   (int64_t)J.delta + pos_bias;
-                uint32_t hh = hit[u];
-                if (hh && idx + __popc(hh) > O.capacity) atomicOr(O.err, kErrCapacity);
-                while (hh) {
-                    const int i = __ffs(hh) - 1;
-                    hh &= hh - 1u;
-                    if (idx < O.capacity) O.positions[idx] = (uint64_t)(s0 + i);
-                    ++idx;
-                }
-                run += __shfl_sync(kFull, inc, 31);
-            }
-        }
     }
 }
 
