@@ -59,6 +59,11 @@ def parse():
                     help="KIND:M[:VARIANT[:N]] — time one search of an N-byte text "
                          "(default 256 MiB) and exit (the small case used for ncu captures)")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--sample", action="store_true",
+                    help="one search per (text, m) of the sweep (15 launches) and exit; the "
+                         "launches an ncu traffic capture measures")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-pairs", type=int, default=8192)
     return ap.parse_args()
 
 
@@ -293,12 +298,95 @@ def profiled_traffic():
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def run_sample(args):
+    """One search per (text, m) of the sweep, with the first (planted) pattern:
+    the launches the committed DRAM-traffic capture covers."""
+    import torch
+    import gen
+    import paper_1209_6449_gb300 as epsm
+    ctx = epsm.Context(0)
+    stream = torch.cuda.current_stream()
+    cap = TEXT_N // 8
+    out = torch.empty(cap, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    rows = []
+    for kind in KINDS:
+        t = torch.empty(TEXT_N, dtype=torch.uint8, device="cuda")
+        gen.TextSpec(kind, 0).device(TEXT_N, t.data_ptr(), stream.cuda_stream)
+        for m in MS:
+            p = gen.mixed_patterns(gen.TextSpec(kind, 0), TEXT_N, m, args.patterns)[0]
+            ctx.search_async(t, p, out, cap, cnt, stream=stream)
+            torch.cuda.synchronize()
+            c = int(cnt.item())
+            rows.append({"text": kind, "m": m, "count": c, "alg_bytes": TEXT_N + 8 * c + 8})
+        del t
+    st = ctx.sync()
+    print(json.dumps({"sample": rows, "mean_alg_bytes": sum(r["alg_bytes"] for r in rows) / len(rows),
+                      "status": st}), flush=True)
+    ctx.close()
+    return 0 if st == 0 else 1
+
+
+def run_batched(ctx, torch, npairs):
+    """The batched-uneven workload: npairs (text, pattern) pairs, text lengths
+    log-uniform in 1 KiB..32 MiB over sigma in {4, 20, 64}, m uniform in 1..32,
+    half planted; one batched launch per step against one launch per pair."""
+    import gen
+    from paper_1209_6449_gb300 import epsm_search_async
+    pairs = gen.batch_pairs(npairs, seed=0)
+    tot = sum(p.n for p in pairs)
+    buf = torch.empty(tot + 16 * npairs, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    texts, off = [], 0
+    for p in pairs:
+        p.spec.device(p.n, buf.data_ptr() + off, s)
+        texts.append((buf.data_ptr() + off, p.n))
+        off += (p.n + 15) // 16 * 16
+    pats = [p.pattern for p in pairs]
+    cap = 1 << 28
+    times = []
+    offs = None
+    for rep in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        offs, out = ctx.search_batch(texts, pats, cap)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        del out
+    batched = min(times[1:])
+    cnts = torch.zeros(npairs, dtype=torch.int64, device="cuda")
+    out2 = torch.empty(cap, dtype=torch.int64, device="cuda")
+    ptimes = []
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, (ptr, n) in enumerate(texts):
+            epsm_search_async(ctx.handle, ptr, n, pats[i], len(pats[i]), out2.data_ptr(), cap,
+                              cnts.data_ptr() + 8 * i, s)
+        torch.cuda.synchronize()
+        ptimes.append(time.perf_counter() - t0)
+    per_pair = min(ptimes)
+    agree = bool((np.diff(offs.astype(np.int64)) == cnts.cpu().numpy()).all())
+    del buf, out2
+    torch.cuda.empty_cache()
+    return {"workload": f"{npairs} pairs, n log-uniform 1 KiB..32 MiB ({tot / 2**30:.2f} GiB), "
+                        "sigma in {4,20,64}, m uniform 1..32, half planted",
+            "queries_per_s": round(npairs / batched, 1), "text_gbs": round(tot / batched / 1e9, 1),
+            "ms": round(batched * 1e3, 3), "per_pair_queries_per_s": round(npairs / per_pair, 1),
+            "per_pair_ms": round(per_pair * 1e3, 3), "speedup_vs_per_pair": round(per_pair / batched, 2),
+            "graph_replay": ctx.batch_uses_graph, "counts_agree_with_per_pair": agree,
+            "timing": "wall clock around the synchronous batched call (upload, launch, offsets "
+                      "download) vs one asynchronous launch per pair and a final synchronize"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.case:
         return run_case(args)
+    if args.sample:
+        return run_sample(args)
 
     import torch
     import gen
@@ -391,6 +479,11 @@ def main():
         cpu = oracle_sample(12.0, None)
     if not args.no_e2e:
         e2e = run_e2e(ctx, pats, args, torch, dev, dist)
+    batched = None
+    if not args.no_batch:
+        del texts, out
+        torch.cuda.empty_cache()
+        batched = run_batched(ctx, torch, args.batch_pairs)
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
@@ -402,9 +495,12 @@ def main():
                              "unit": "GB/s", "frac": round(achieved / peak, 4),
                              "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                              "kernel": "scan_kernel (all variants; algorithmic bytes = n + 8*occ + 8 per launch)",
-                             "traffic": traffic.get("bytes_per_launch") if traffic else None},
+                             "traffic": traffic.get("bytes_per_launch") if traffic else None,
+                             "traffic_note": (traffic.get("note") if traffic else
+                                              "null: no ncu capture of the current kernel sources")},
                 "cpu_baseline": cpu,
                 "e2e": e2e,
+                "batched": batched,
                 "gpu_launches": launches,
                 "clocks": clocks.summary(t_wall0, t_wall1),
                 "occurrences_per_step": occ_total}

@@ -141,12 +141,20 @@ def epsm_search_static(text: int, n: int, pattern: bytes, m: int, positions: int
 class Context:
     """One library context on one CUDA device (not thread-safe)."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, tuning: str | None = "default"):
+        """``tuning``: "default" installs the measured variant table shipped
+        next to this file (if present); a path installs that table; None keeps
+        the library's built-in choice."""
         import torch
         self._torch = torch
         self.device = device
         self.handle = epsm_create(device)
         self._count = torch.zeros(1, dtype=torch.int64, device=f"cuda:{device}")
+        if tuning is not None:
+            from . import autotune
+            table = autotune.load() if tuning == "default" else autotune.load(tuning)
+            if table is not None:
+                autotune.apply(self, table)
 
     def close(self):
         if self.handle:

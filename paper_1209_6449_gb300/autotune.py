@@ -1,0 +1,95 @@
+"""Autotuner for the per-m kernel variant (the EPSM dispatcher of Section 3
+chooses its procedure by m; on the GPU the choice is measured, not fixed).
+
+For every pattern length m it times each variant that covers m on texts of a
+few alphabet sizes (uniform random bytes over sigma symbols, with patterns
+copied from the text) and keeps the variant with the smallest total time.  The
+table is written as JSON and installed into a context with ``apply``.
+``Context`` loads ``tuning.json`` next to this file when it exists.
+
+Run on the target GPU:  python -m paper_1209_6449_gb300.autotune [out.json]
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+from ._native import VARIANT_BLOCK8, VARIANT_DIRECT, VARIANT_NAMES, VARIANT_PREFIX4, VARIANT_PREFIX8
+
+COVER = {VARIANT_DIRECT: range(1, 5), VARIANT_PREFIX4: range(4, 16),
+         VARIANT_PREFIX8: range(8, 16), VARIANT_BLOCK8: range(15, 33)}
+DEFAULT_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
+
+
+def variants_for(m: int):
+    return [v for v, r in COVER.items() if m in r]
+
+
+def autotune(ctx, n: int = 64 << 20, sigmas=(4, 20, 64), ms=range(1, 33), reps: int = 3,
+             patterns: int = 4, seed: int = 0) -> dict:
+    """Measure every (m, variant) and return the tuning table."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    texts = []
+    for sigma in sigmas:
+        t = torch.randint(65, 65 + sigma, (n,), generator=g, dtype=torch.uint8)
+        texts.append(t.cuda())
+    cap = n // 2
+    out = torch.empty(cap, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    table, detail = {}, {}
+    for m in ms:
+        best, best_t = None, None
+        times = {}
+        for v in variants_for(m):
+            total = 0.0
+            for t in texts:
+                offs = torch.randint(0, n - m, (patterns,), generator=g).tolist()
+                pats = [bytes(t[o:o + m].cpu().numpy()) for o in offs]
+                for p in pats:  # warm-up
+                    ctx.search_async(t, p, out, cap, cnt, variant=v)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    for p in pats:
+                        ctx.search_async(t, p, out, cap, cnt, variant=v)
+                e1.record()
+                torch.cuda.synchronize()
+                total += e0.elapsed_time(e1) / (reps * len(pats))
+            times[VARIANT_NAMES[v]] = round(total, 4)
+            if best_t is None or total < best_t:
+                best, best_t = v, total
+        table[m] = best
+        detail[m] = times
+    if ctx.sync() != 0:
+        raise RuntimeError("device error during autotuning")
+    return {"variant": {str(m): v for m, v in table.items()},
+            "names": {str(m): VARIANT_NAMES[v] for m, v in table.items()},
+            "ms_per_search": {str(m): d for m, d in detail.items()},
+            "text_bytes": n, "sigmas": list(sigmas), "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+
+
+def apply(ctx, table: dict) -> None:
+    for m, v in table["variant"].items():
+        ctx.set_variant(int(m), int(v))
+
+
+def load(path: str = DEFAULT_PATH):
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f)
+
+
+if __name__ == "__main__":
+    from . import Context
+    ctx = Context(0)
+    res = autotune(ctx)
+    out = sys.argv[1] if len(sys.argv) > 1 else DEFAULT_PATH
+    with open(out, "w") as f:
+        json.dump(res, f, indent=1)
+    print(json.dumps(res["names"]))

@@ -29,7 +29,7 @@ using namespace epsm;
 namespace {
 
 int default_variant(uint32_t m) {
-    if (m <= 3) return V_DIRECT;
+    if (m <= 4) return V_DIRECT;
     if (m <= 7) return V_PREFIX4;
     if (m <= 14) return V_PREFIX8;
     return V_BLOCK8;

@@ -244,35 +244,19 @@ __device__ __forceinline__ void emit_range(const BatchParams &P, const Header &H
                 ++jcur;
             }
         }
-        uint32_t todo = __ballot_sync(kFull, c != 0u);
+        const uint32_t todo = __ballot_sync(kFull, c != 0u);
         if (todo && H.emit) {
-            int j = __ffs(todo) - 1;
-            todo &= todo - 1u;
-            uint64_t sj = sb + (uint64_t)w * 32u + (uint64_t)j;
-            uint2 cur = load_masks(P.seg_mask, sj, lane);
-            for (;;) {
-                const uint64_t ej = __shfl_sync(kFull, excl, j);
-                int jn = -1;
-                uint64_t sn = 0;
-                uint2 nxt = make_uint2(0u, 0u);
-                if (todo) {
-                    jn = __ffs(todo) - 1;
-                    todo &= todo - 1u;
-                    sn = sb + (uint64_t)w * 32u + (uint64_t)jn;
-                    nxt = load_masks(P.seg_mask, sn, lane);
-                }
-                const uint64_t stg = sj / kConsumerWarps;
-                while (wj + 1u < H.njobs && P.jobs[wj + 1u].stage0 <= stg) ++wj;
-                const JobDesc &D = P.jobs[wj];
-                const int64_t s0 = (int64_t)(((stg - D.stage0) * kStageChunks +
-                                              (sj % kConsumerWarps) * kSegChunks) * 16u) +
-                                   D.off - (int64_t)D.job.delta;
-                emit_segment(H.positions, H.capacity, P.err, s0, ej, cur, S.emit_stage[w], lane);
-                if (jn < 0) break;
-                j = jn;
-                sj = sn;
-                cur = nxt;
-            }
+            emit_list(todo, sb + (uint64_t)w * 32u, excl, P.seg_mask, lane,
+                      [&](uint64_t sj, uint64_t ej, uint2 packed) {
+                          const uint64_t stg = sj / kConsumerWarps;
+                          while (wj + 1u < H.njobs && P.jobs[wj + 1u].stage0 <= stg) ++wj;
+                          const JobDesc &D = P.jobs[wj];
+                          const int64_t s0 = (int64_t)(((stg - D.stage0) * kStageChunks +
+                                                        (sj % kConsumerWarps) * kSegChunks) * 16u) +
+                                             D.off - (int64_t)D.job.delta;
+                          emit_segment(H.positions, H.capacity, P.err, s0, ej, packed,
+                                       S.emit_stage[w], lane);
+                      });
         }
         base += btotal;
         consumer_sync();  // batch_excl is rewritten by the next batch

@@ -383,6 +383,41 @@ __device__ __forceinline__ uint2 load_masks(const uint16_t *seg_mask, uint64_t s
     return reinterpret_cast<const uint2 *>(seg_mask + seg * kSegChunks)[lane];
 }
 
+// Emits the segments of a warp's batch listed in `todo` (bit j: segment
+// first + j has hits; lane j holds its exclusive output offset in `excl`).  The
+// masks of up to kEmitAhead segments are loaded together before they are
+// emitted, so the L2 latency of the mask loads is paid once per group.
+constexpr int kEmitAhead = 4;
+
+template <typename EmitFn>
+__device__ __forceinline__ void emit_list(uint32_t todo, uint64_t first, uint64_t excl,
+                                          const uint16_t *seg_mask, int lane, EmitFn &&emit) {
+    while (todo) {
+        int js[kEmitAhead];
+        uint2 mk[kEmitAhead];
+#pragma unroll
+        for (int k = 0; k < kEmitAhead; ++k) {
+            js[k] = -1;
+            if (todo) {
+                js[k] = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                mk[k] = load_masks(seg_mask, first + (uint64_t)js[k], lane);
+            }
+        }
+        // one copy of the emit code (not unrolled): it is large
+#pragma unroll 1
+        for (int k = 0; k < kEmitAhead; ++k) {
+            int jk = js[0];
+            uint2 mkk = mk[0];
+#pragma unroll
+            for (int q = 1; q < kEmitAhead; ++q)
+                if (q == k) { jk = js[q]; mkk = mk[q]; }
+            if (jk < 0) break;
+            emit(first + (uint64_t)jk, __shfl_sync(kFull, excl, jk), mkk);
+        }
+    }
+}
+
 // Phase 3 for the consumer warps: block-ordered prefix of the segment counts
 // in batches of 256 segments, and emission of the segments with hits.  Each
 // warp walks its segments with hits and loads the next one's masks before it
@@ -408,32 +443,14 @@ __device__ __forceinline__ void emit_block(const StreamParams &P, StreamSmem &S,
         }
         consumer_sync();
         const uint64_t excl = base + wbase + inc - c;
-        uint32_t todo = __ballot_sync(kFull, c != 0u);
-        if (todo) {
-            int j = __ffs(todo) - 1;
-            todo &= todo - 1u;
-            uint64_t sj = sb + (uint64_t)w * 32u + (uint64_t)j;
-            uint2 cur = load_masks(P.seg_mask, sj, lane);
-            for (;;) {
-                const uint64_t ej = __shfl_sync(kFull, excl, j);
-                int jn = -1;
-                uint64_t sn = 0;
-                uint2 nxt = make_uint2(0u, 0u);
-                if (todo) {
-                    jn = __ffs(todo) - 1;
-                    todo &= todo - 1u;
-                    sn = sb + (uint64_t)w * 32u + (uint64_t)jn;
-                    nxt = load_masks(P.seg_mask, sn, lane);
-                }
-                const int64_t s0 =
-                    (int64_t)(sj * kSegChunks * 16u) + OFF - (int64_t)P.job.delta;
-                emit_segment(P.positions, P.capacity, P.err, s0, ej, cur, S.emit_stage[w], lane);
-                if (jn < 0) break;
-                j = jn;
-                sj = sn;
-                cur = nxt;
-            }
-        }
+        const uint32_t todo = __ballot_sync(kFull, c != 0u);
+        const int64_t seg_pos0 = OFF - (int64_t)P.job.delta;
+        emit_list(todo, sb + (uint64_t)w * 32u, excl, P.seg_mask, lane,
+                  [&](uint64_t sj, uint64_t ej, uint2 packed) {
+                      const int64_t s0 = (int64_t)(sj * kSegChunks * 16u) + seg_pos0;
+                      emit_segment(P.positions, P.capacity, P.err, s0, ej, packed,
+                                   S.emit_stage[w], lane);
+                  });
         base += btotal;
     }
 }
