@@ -14,13 +14,14 @@
 
 #include <algorithm>
 #include <mutex>
-#include <unordered_map>
+#include <map>
+#include <utility>
 #include <vector>
 
 #include "epsm.h"
 #include "epsm_kernels.cuh"
 #include "epsm_stream.cuh"
-#include "epsm_batch.cuh"
+#include "epsm_group.cuh"
 
 using namespace epsm;
 
@@ -77,22 +78,34 @@ SearchJob make_job(const uint8_t *text, uint64_t n, const Pattern &pat) {
 // (header/jobs upload -> table build -> batched scan -> offsets download),
 // built once per capacity and replayed for every batch that fits.
 struct BatchRes {
-    uint8_t *hstage = nullptr;  // pinned: Header, then JobDesc[cap]
+    uint8_t *hstage = nullptr;  // pinned: Header | JobDesc[] | GroupDesc[] | uint32 group_jobs[]
     uint8_t *dstage = nullptr;
     uint64_t *hoff = nullptr;   // pinned: job offsets + total
     uint64_t *doff = nullptr;
-    uint8_t *tables = nullptr;
-    uint32_t cap = 0;           // jobs
+    uint8_t *tables = nullptr;  // cap block-variant tables
+    uint8_t *comb = nullptr;    // comb_cap shared tables
+    unsigned long long *rt = nullptr;  // per-range hit totals of the batched launch
+    uint32_t cap = 0;           // jobs (and groups)
+    uint32_t comb_cap = 0;
     cudaGraph_t graph = nullptr;     // kept: its node handles address the exec's copies
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t up = nullptr, down = nullptr;
     uint64_t graph_seg_cap = 0;      // scratch size the graph was built with
-    uint64_t *graph_positions = nullptr;
     bool graph_failed = false;       // a build failed once: launch directly
     int grid = 0;
 };
 
-constexpr size_t kBatchHdrBytes = 64;  // Header, padded to keep JobDesc aligned
+constexpr size_t kBatchHdrBytes = 128;  // Header, padded to keep JobDesc aligned
+
+size_t batch_jobs_off() { return kBatchHdrBytes; }
+size_t align16(size_t x) { return (x + 15u) & ~(size_t)15u; }
+// Staging: Header | JobDesc[nj] | GroupDesc[ng] | uint32 group_jobs[nj], each
+// part 16-byte aligned, packed after the jobs actually used (the upload is
+// only as large as the batch); sized for cap jobs and cap groups.
+size_t batch_stage_bytes(uint32_t cap) {
+    return kBatchHdrBytes + align16((size_t)cap * sizeof(group::JobDesc)) +
+           align16((size_t)cap * sizeof(group::GroupDesc)) + (size_t)cap * sizeof(uint32_t);
+}
 
 }  // namespace
 
@@ -287,53 +300,85 @@ void free_batch(BatchRes &R) {
     if (R.hoff) cudaFreeHost(R.hoff);
     if (R.doff) cudaFree(R.doff);
     if (R.tables) cudaFree(R.tables);
+    if (R.comb) cudaFree(R.comb);
+    if (R.rt) cudaFree(R.rt);
     R = BatchRes();
 }
 
 int batch_grid(int sms) {
     static int per_sm = 0;
     if (per_sm == 0) {
-        const size_t smem = sizeof(batch::BatchSmem);
-        if (cudaFuncSetAttribute(batch_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        const size_t smem = sizeof(group::Smem);
+        if (cudaFuncSetAttribute(group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return 0;
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_stream_kernel,
-                                                          stream::kThreadsStream, smem) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, group_kernel, stream::kThreadsStream,
+                                                          smem) != cudaSuccess)
             return 0;
         per_sm = std::max(1, std::min(b, stream::kMaxBlocksPerSm));
     }
     return (int)std::min<uint64_t>((uint64_t)sms * per_sm, stream::kMaxBlocks);
 }
 
-epsm_status ensure_batch(epsm_ctx *c, uint32_t njobs, cudaStream_t s) {
+void drop_graph(BatchRes &R) {
+    if (R.exec) cudaGraphExecDestroy(R.exec);
+    if (R.graph) cudaGraphDestroy(R.graph);
+    R.exec = nullptr;
+    R.graph = nullptr;
+}
+
+epsm_status ensure_batch(epsm_ctx *c, uint32_t njobs, uint32_t ncomb, cudaStream_t s) {
     BatchRes &R = c->batch;
-    if (R.hstage && njobs <= R.cap) return EPSM_OK;
-    const uint32_t cap = std::max<uint32_t>({njobs, R.cap * 2u, 64u});
-    CK(cudaStreamSynchronize(s));
-    CK(cudaDeviceSynchronize());
-    free_batch(R);
-    const size_t stage_bytes = kBatchHdrBytes + (size_t)cap * sizeof(batch::JobDesc);
-    CK(cudaMallocHost((void **)&R.hstage, stage_bytes));
-    CK(cudaMalloc((void **)&R.dstage, stage_bytes));
-    CK(cudaMallocHost((void **)&R.hoff, ((size_t)cap + 1) * sizeof(uint64_t)));
-    CK(cudaMalloc((void **)&R.doff, ((size_t)cap + 1) * sizeof(uint64_t)));
-    CK(cudaMalloc((void **)&R.tables, (size_t)cap * batch::kTableBytes));
-    R.cap = cap;
+    if (!R.hstage || njobs > R.cap) {
+        const uint32_t cap = std::max<uint32_t>({njobs, R.cap * 2u, 64u});
+        CK(cudaStreamSynchronize(s));
+        CK(cudaDeviceSynchronize());
+        drop_graph(R);
+        if (R.hstage) CK(cudaFreeHost(R.hstage));
+        if (R.dstage) CK(cudaFree(R.dstage));
+        if (R.hoff) CK(cudaFreeHost(R.hoff));
+        if (R.doff) CK(cudaFree(R.doff));
+        if (R.tables) CK(cudaFree(R.tables));
+        R.hstage = R.dstage = R.tables = nullptr;
+        R.hoff = R.doff = nullptr;
+        R.cap = 0;
+        const size_t sb = batch_stage_bytes(cap);
+        CK(cudaMallocHost((void **)&R.hstage, sb));
+        CK(cudaMalloc((void **)&R.dstage, sb));
+        CK(cudaMallocHost((void **)&R.hoff, ((size_t)cap + 1) * sizeof(uint64_t)));
+        CK(cudaMalloc((void **)&R.doff, ((size_t)cap + 1) * sizeof(uint64_t)));
+        CK(cudaMalloc((void **)&R.tables, (size_t)cap * group::kTableBytes));
+        if (!R.rt)
+            CK(cudaMalloc((void **)&R.rt, (size_t)group::kRangesPerBlock * stream::kMaxBlocks *
+                                              sizeof(unsigned long long)));
+        R.cap = cap;
+    }
+    if (ncomb > R.comb_cap) {
+        const uint32_t cc = std::max<uint32_t>({ncomb, R.comb_cap * 2u, 4u});
+        CK(cudaStreamSynchronize(s));
+        drop_graph(R);
+        if (R.comb) CK(cudaFree(R.comb));
+        R.comb = nullptr;
+        R.comb_cap = 0;
+        CK(cudaMalloc((void **)&R.comb, (size_t)cc * sizeof(group::SharedTable)));
+        R.comb_cap = cc;
+    }
     return EPSM_OK;
 }
 
-batch::BatchParams batch_params(epsm_ctx *c) {
+group::Params batch_params(epsm_ctx *c) {
     BatchRes &R = c->batch;
-    batch::BatchParams p;
+    group::Params p;
     memset(&p, 0, sizeof(p));
-    p.hdr = reinterpret_cast<const batch::Header *>(R.dstage);
-    p.jobs = reinterpret_cast<const batch::JobDesc *>(R.dstage + kBatchHdrBytes);
+    p.hdr = reinterpret_cast<const group::Header *>(R.dstage);
+    p.jobs = reinterpret_cast<const group::JobDesc *>(R.dstage + batch_jobs_off());
+    p.comb = reinterpret_cast<group::SharedTable *>(R.comb);
     p.tables = R.tables;
     p.offsets = R.doff;
     p.seg_count = c->seg_count;
     p.seg_mask = c->seg_mask;
-    p.range_total = c->range_total;
+    p.range_total = R.rt;
     p.err = &c->misc->err;
     p.misc = c->misc;
     return p;
@@ -342,16 +387,16 @@ batch::BatchParams batch_params(epsm_ctx *c) {
 constexpr int kTableGrid = 256;
 
 // The four steps of a batched submission, enqueued on s.
-cudaError_t enqueue_batch(epsm_ctx *c, const batch::BatchParams &p, size_t up, size_t down,
+cudaError_t enqueue_batch(epsm_ctx *c, const group::Params &p, size_t up, size_t down,
                           cudaStream_t s) {
     BatchRes &R = c->batch;
     cudaError_t e = cudaMemcpyAsync(R.dstage, R.hstage, up, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
-    batch::build_tables_kernel<<<kTableGrid, 256, 0, s>>>(p);
+    group::build_group_tables_kernel<<<kTableGrid, 256, 0, s>>>(p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     void *args[] = {(void *)&p};
-    e = cudaLaunchCooperativeKernel((const void *)batch_stream_kernel, dim3(R.grid),
-                                    dim3(stream::kThreadsStream), args, sizeof(batch::BatchSmem), s);
+    e = cudaLaunchCooperativeKernel((const void *)group_kernel, dim3(R.grid),
+                                    dim3(stream::kThreadsStream), args, sizeof(group::Smem), s);
     if (e != cudaSuccess) return e;
     return cudaMemcpyAsync(R.hoff, R.doff, down, cudaMemcpyDeviceToHost, s);
 }
@@ -362,16 +407,9 @@ cudaError_t enqueue_batch(epsm_ctx *c, const batch::BatchParams &p, size_t up, s
 // launches in use (the reason is kept in the context's error string).
 void build_batch_graph(epsm_ctx *c) {
     BatchRes &R = c->batch;
-    if (R.exec) {
-        cudaGraphExecDestroy(R.exec);
-        R.exec = nullptr;
-    }
-    if (R.graph) {
-        cudaGraphDestroy(R.graph);
-        R.graph = nullptr;
-    }
-    const batch::BatchParams p = batch_params(c);  // node arguments are copied when added
-    const size_t up = kBatchHdrBytes + (size_t)R.cap * sizeof(batch::JobDesc);
+    drop_graph(R);
+    const group::Params p = batch_params(c);  // node arguments are copied when added
+    const size_t up = batch_stage_bytes(R.cap);
     const size_t down = ((size_t)R.cap + 1) * sizeof(uint64_t);
     cudaGraph_t g = nullptr;
     cudaGraphNode_t n_up = nullptr, n_tab = nullptr, n_scan = nullptr, n_down = nullptr;
@@ -387,7 +425,7 @@ void build_batch_graph(epsm_ctx *c) {
         cudaKernelNodeParams kp;
         memset(&kp, 0, sizeof(kp));
         void *args[] = {(void *)&p};
-        kp.func = (void *)batch::build_tables_kernel;
+        kp.func = (void *)group::build_group_tables_kernel;
         kp.gridDim = dim3(kTableGrid);
         kp.blockDim = dim3(256);
         kp.kernelParams = args;
@@ -398,10 +436,10 @@ void build_batch_graph(epsm_ctx *c) {
         cudaKernelNodeParams kp;
         memset(&kp, 0, sizeof(kp));
         void *args[] = {(void *)&p};
-        kp.func = (void *)batch_stream_kernel;
+        kp.func = (void *)group_kernel;
         kp.gridDim = dim3(R.grid);
         kp.blockDim = dim3(stream::kThreadsStream);
-        kp.sharedMemBytes = sizeof(batch::BatchSmem);
+        kp.sharedMemBytes = sizeof(group::Smem);
         kp.kernelParams = args;
         e = cudaGraphAddKernelNode(&n_scan, g, &n_tab, 1, &kp);
         if (e == cudaSuccess) {
@@ -435,52 +473,161 @@ void build_batch_graph(epsm_ctx *c) {
     R.graph_seg_cap = c->seg_cap;
 }
 
+// Window stride K of a pattern in the shared filter of its text's group (0:
+// searched alone with its own variant): the largest power of two with
+// K + W - 1 <= m, W = 4 for m <= 10 (K at most 4) and 8 for m >= 11 (K at
+// most 8).
+uint32_t shared_stride(uint32_t m) {
+    if (m <= 4) return 0;
+    if (m <= 6) return 2;
+    if (m <= 14) return 4;
+    return 8;
+}
+
+// Pairs on the same text (same pointer and length) are searched in shared
+// passes: one group per text (more if its patterns exceed the per-group
+// limits), with a shared filter over its patterns of stride K > 0 and the
+// others run one by one on the staged bytes.
 epsm_status batch_impl(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts,
                        const uint64_t *ns, const uint8_t *const *patterns, const uint32_t *ms,
                        uint64_t *positions, uint64_t capacity, uint64_t *offsets,
                        cudaStream_t s) {
-    epsm_status st;
-    if ((st = ensure_batch(c, npairs, s)) != EPSM_OK) return st;
-    BatchRes &R = c->batch;
-    if (R.grid == 0) R.grid = batch_grid(c->sms);
-    if (R.grid == 0) return EPSM_ERR_CUDA;
-    batch::Header &H = *reinterpret_cast<batch::Header *>(R.hstage);
-    batch::JobDesc *jobs = reinterpret_cast<batch::JobDesc *>(R.hstage + kBatchHdrBytes);
-    uint32_t nj = 0, nt = 0;
-    uint64_t stage0 = 0;
-    for (uint32_t i = 0; i < npairs; ++i) {
-        const int v = c->variant[ms[i]];
-        const SearchJob J = make_job(texts[i], ns[i], pack_pattern(patterns[i], ms[i]));
-        const uint64_t nst = stages_for(J.delta, ns[i], ms[i], v);
-        if (nst == 0) continue;
-        batch::JobDesc &D = jobs[nj++];
-        memset(&D, 0, sizeof(D));
-        D.job = J;
-        D.stage0 = stage0;
-        D.nstages = nst;
-        D.chunk_full0 = (J.delta + 15u) / 16u;
-        D.chunk_full1 = J.lim / 16u;
-        D.variant = (uint32_t)v;
-        D.table = v == V_BLOCK8 ? nt++ : batch::kNoTable;
-        D.pair = i;
-        D.off = variant_offset(v);
-        stage0 += nst;
+    using namespace group;
+    // texts shared by several pairs
+    using TextKey = std::pair<uintptr_t, uint64_t>;  // (start, length): same view
+    std::map<TextKey, std::vector<uint32_t>> by_text;
+    std::vector<TextKey> text_order;
+    for (uint32_t j = 0; j < npairs; ++j) {
+        const TextKey key((uintptr_t)texts[j], ns[j]);
+        auto it = by_text.find(key);
+        if (it == by_text.end()) {
+            by_text.emplace(key, std::vector<uint32_t>{j});
+            text_order.push_back(key);
+        } else {
+            it->second.push_back(j);
+        }
     }
-    memset(&H, 0, sizeof(H));
-    H.njobs = nj;
-    H.ntables = nt;
-    H.nstages = stage0;
-    H.range_stages = std::max<uint64_t>(1, (stage0 + R.grid - 1) / R.grid);
-    H.capacity = capacity;
-    H.positions = positions;
-    H.emit = capacity > 0 ? 1u : 0u;
+    std::vector<uint32_t> kstr(npairs, 0u);
+    std::vector<uint8_t> multi(npairs, 0);
+    for (const TextKey &key : text_order) {
+        const auto &v = by_text[key];
+        if (v.size() < 2) continue;
+        for (uint32_t j : v) {
+            kstr[j] = shared_stride(ms[j]);
+            multi[j] = 1;
+        }
+    }
+    // jobs (pairs with at least one stage), in pair order; shared patterns use
+    // the numbering with start offset 0 of the window variants
+    std::vector<int32_t> jidx(npairs, -1);
+    std::vector<JobDesc> kept;
+    kept.reserve(npairs);
+    uint64_t jst = 0;
+    uint32_t ntab = 0;
+    for (uint32_t i = 0; i < npairs; ++i) {
+        const uint32_t m = ms[i];
+        JobDesc D;
+        memset(&D, 0, sizeof(D));
+        D.job = make_job(texts[i], ns[i], pack_pattern(patterns[i], m));
+        // shared patterns are numbered like the window variants (offset 0);
+        // short patterns of a shared text run the direct compare
+        D.variant = (uint32_t)(kstr[i] ? V_PREFIX4 : multi[i] ? V_DIRECT : c->variant[m]);
+        const uint64_t nst = stages_for(D.job.delta, ns[i], m, (int)D.variant);
+        if (nst == 0) continue;
+        D.pair = i;
+        D.stage0 = jst;
+        D.nstages = nst;
+        D.off = variant_offset((int)D.variant);
+        D.kstride = kstr[i];
+        D.table = (!kstr[i] && D.variant == (uint32_t)V_BLOCK8) ? ntab++ : kNone;
+        jidx[i] = (int32_t)kept.size();
+        kept.push_back(D);
+        jst += nst;
+    }
+    const uint32_t nj = (uint32_t)kept.size();
     if (nj == 0) {
         for (uint32_t i = 0; i <= npairs; ++i) offsets[i] = 0;
         return EPSM_OK;
     }
-    if ((st = ensure_stream_scratch(c, stage0, s)) != EPSM_OK) return st;
+    // groups: per text, shared patterns up to kMaxShared / kMaxEnt entries and
+    // individual ones up to kIndivMax per group
+    std::vector<GroupDesc> groups;
+    std::vector<uint32_t> gjobs;
+    gjobs.reserve(nj);
+    uint32_t ncomb = 0;
+    uint64_t gst = 0;
+    for (const TextKey &key : text_order) {
+        std::vector<uint32_t> sh, ind;
+        for (uint32_t pi : by_text[key]) {
+            if (jidx[pi] < 0) continue;
+            (kstr[pi] ? sh : ind).push_back((uint32_t)jidx[pi]);
+        }
+        size_t ps = 0, pi = 0;
+        while (ps < sh.size() || pi < ind.size()) {
+            GroupDesc G;
+            memset(&G, 0, sizeof(G));
+            G.job0 = (uint32_t)gjobs.size();
+            uint64_t nst = 0;
+            uint32_t k8 = 0, k4 = 0;
+            while (ps < sh.size() && G.nshared < (uint32_t)kMaxShared &&
+                   G.nent + kept[sh[ps]].kstride <= (uint32_t)kMaxEnt) {
+                JobDesc &D = kept[sh[ps++]];
+                D.ent0 = G.nent;
+                G.nent += D.kstride;
+                ++G.nshared;
+                gjobs.push_back((uint32_t)(&D - kept.data()));
+                nst = std::max(nst, D.nstages);
+                uint32_t &k = D.job.pat.m >= kW8Min ? k8 : k4;
+                k = k ? std::min(k, D.kstride) : D.kstride;
+            }
+            while (pi < ind.size() && G.nindiv < (uint32_t)kIndivMax) {
+                const uint32_t jj = ind[pi++];
+                ++G.nindiv;
+                gjobs.push_back(jj);
+                nst = std::max(nst, kept[jj].nstages);
+            }
+            const JobDesc &D0 = kept[gjobs[G.job0]];
+            G.text = D0.job;
+            G.chunk_full0 = (D0.job.delta + 15u) / 16u;
+            G.chunk_full1 = D0.job.lim / 16u;
+            G.gstage0 = gst;
+            G.nstages = nst;
+            G.cfg = k8 | (k4 << 8);
+            G.comb = G.nshared ? ncomb++ : kNone;
+            gst += nst;
+            groups.push_back(G);
+        }
+    }
+    const uint32_t ng = (uint32_t)groups.size();
+    epsm_status st;
+    if ((st = ensure_batch(c, std::max(nj, ng), ncomb, s)) != EPSM_OK) return st;
+    BatchRes &R = c->batch;
+    if (R.grid == 0) R.grid = batch_grid(c->sms);
+    if (R.grid == 0) return EPSM_ERR_CUDA;
+    Header &H = *reinterpret_cast<Header *>(R.hstage);
+    memset(&H, 0, sizeof(H));
+    H.ngroups = ng;
+    H.njobs = nj;
+    H.gstages = gst;
+    H.jstages = jst;
+    // emit ranges: up to kRangesPerBlock per block, dealt round-robin so that
+    // dense and sparse patterns' stages spread over all blocks
+    const uint64_t nr_want = std::min<uint64_t>(jst, (uint64_t)kRangesPerBlock * (uint64_t)R.grid);
+    H.range_stages = (jst + nr_want - 1) / nr_want;
+    H.nranges = (uint32_t)((jst + H.range_stages - 1) / H.range_stages);
+    H.capacity = capacity;
+    H.positions = positions;
+    H.emit = capacity > 0 ? 1u : 0u;
+    const size_t goff = batch_jobs_off() + align16((size_t)nj * sizeof(JobDesc));
+    const size_t gjoff = goff + align16((size_t)ng * sizeof(GroupDesc));
+    H.groups = reinterpret_cast<const GroupDesc *>(R.dstage + goff);
+    H.group_jobs = reinterpret_cast<const uint32_t *>(R.dstage + gjoff);
+    memcpy(R.hstage + batch_jobs_off(), kept.data(), nj * sizeof(JobDesc));
+    memcpy(R.hstage + goff, groups.data(), ng * sizeof(GroupDesc));
+    memcpy(R.hstage + gjoff, gjobs.data(), gjobs.size() * sizeof(uint32_t));
+    if ((st = ensure_stream_scratch(c, jst, s)) != EPSM_OK) return st;
     if ((st = order_after_previous(c, s)) != EPSM_OK) return st;
-    const size_t up = kBatchHdrBytes + (size_t)nj * sizeof(batch::JobDesc);
+    const size_t up = gjoff + gjobs.size() * sizeof(uint32_t);
     const size_t down = ((size_t)nj + 1) * sizeof(uint64_t);
     if (!R.graph_failed && (!R.exec || R.graph_seg_cap != c->seg_cap)) build_batch_graph(c);
     bool launched = false;
@@ -501,12 +648,11 @@ epsm_status batch_impl(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts
     if ((st = mark_done(c, s)) != EPSM_OK) return st;
     uint32_t err = 0;
     if ((st = read_misc(c, s, &err)) != EPSM_OK) return st;
-    // job offsets -> pair offsets; pairs without stages (n < m) own an empty
-    // range at the next pair's offset
-    std::vector<uint64_t> by_pair(npairs, ~0ull);
-    for (uint32_t j = 0; j < nj; ++j) by_pair[jobs[j].pair] = R.hoff[j];
+    // job offsets -> pair offsets; pairs without stages own an empty range at
+    // the next pair's offset
     offsets[npairs] = R.hoff[nj];
-    for (uint32_t i = npairs; i-- > 0;) offsets[i] = by_pair[i] != ~0ull ? by_pair[i] : offsets[i + 1];
+    for (uint32_t i = npairs; i-- > 0;)
+        offsets[i] = jidx[i] >= 0 ? R.hoff[jidx[i]] : offsets[i + 1];
     if (err & kErrTimeout) return EPSM_ERR_TIMEOUT;
     return offsets[npairs] > capacity ? EPSM_ERR_CAPACITY : EPSM_OK;
 }

@@ -1,0 +1,855 @@
+// Batched search with shared text passes: many (text, pattern) pairs in one
+// cooperative persistent launch, where all pairs on the same text form a group
+// whose stages are loaded once and searched for every pattern of the group.
+//
+// Shared filter.  The patterns of a group with m >= 5 share one exact-match
+// hash table of pattern windows, a multi-pattern form of the block
+// fingerprint of Section 3.4.  A pattern of length m contributes the windows
+// p[j..j+W) for j = 0..K-1, with width W = 4 (m <= 10) or 8 (m >= 11) and
+// stride K the largest power of two <= m - W + 1 (at most 4 for W = 4, 8 for
+// W = 8).  Every occurrence at s contains exactly one text window that starts
+// at a multiple of K in [s, s+K), at j = that start - s, so looking up the
+// text windows at the multiples of K finds each occurrence exactly once.  A
+// lane holding chunk c (starts 16c .. 16c+15) looks up the windows at 16c + q
+// for q = 0..16, q a multiple of the group's smallest stride of that width,
+// and accepts an entry (i, j, K) when K divides q and 0 <= q - j <= 15, so
+// the start falls in its own chunk.
+// The table lives in shared memory: 4096 head slots, each 0 or a 16-bit tag
+// of the window's hash plus the index of its first entry (tag 0 marks a slot
+// shared by several entries), and the entries {window, pattern, j, K, next}.
+// A window whose slot is empty or carries another tag is rejected with one
+// shared load; the chains of the others are compared exactly after the
+// chunk's lookups and a window match is checked in full (from the staged
+// bytes where they cover it).
+//
+// Confirmed hits go to a per-warp list; each pattern's segment count and masks
+// are then written in the layout of the single search (one segment numbering
+// per pattern, chunk bit i <-> start 16c + i), so the ordered emit, the range
+// totals and the pair offsets are those of the single search.  A pattern whose
+// hits do not fit in the list is redone alone on that segment with a prefix
+// filter (dense hits).  Patterns with m <= 4 and patterns alone on their text
+// run their own single-search variant on the staged bytes.
+//
+// Phases: claim group stages dynamically and stream them through a ring of
+// stage buffers; grid barrier; per-block prefix over range totals; ordered emit
+// of the block's range of pattern stages (see epsm_stream.cuh).  Every wait is
+// bounded in time.
+#pragma once
+
+#include "epsm_stream.cuh"
+
+namespace epsm {
+namespace group {
+
+using namespace stream;
+
+constexpr int kRing = 3;                 // stages in flight per block
+constexpr int kSlotBits = 12;
+constexpr int kSlots = 1 << kSlotBits;   // head slots of the shared table
+constexpr int kMaxEnt = 512;             // window entries per group
+constexpr int kMaxShared = 128;          // shared-filter patterns per group
+constexpr int kIndivMax = 64;            // single-variant patterns per group
+constexpr int kHitCap = 256;             // confirmed hits per warp and stage
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kEndChain = 0xFFFFu;
+constexpr uint32_t kW8Min = 11;          // patterns this long use 8-byte windows
+constexpr int kRangesPerBlock = 32;      // emit ranges per block (dealt round-robin)
+
+struct JobDesc {
+    SearchJob job;         // text view and pattern
+    uint64_t stage0;       // first stage of the pair in the per-pattern numbering
+    uint64_t nstages;      // > 0
+    uint32_t variant;      // single-search variant (individual patterns)
+    uint32_t table;        // block-variant table (kNone if unused)
+    uint32_t pair;         // index in the caller's arrays
+    int32_t off;           // start offset of bit 0 of a chunk (-7 for the block variant)
+    uint32_t kstride;      // shared patterns: window stride K (0: individual pattern)
+    uint32_t ent0;         // shared patterns: index of its first table entry
+};
+
+struct GroupDesc {
+    SearchJob text;        // text view (pattern unused)
+    uint64_t chunk_full0, chunk_full1;
+    uint64_t gstage0;      // first stage of the group in the group numbering
+    uint64_t nstages;      // max over the group's patterns
+    uint32_t job0;         // group_jobs[job0 ..]: shared patterns, then individual ones
+    uint32_t nshared;
+    uint32_t nindiv;
+    uint32_t nent;         // table entries
+    uint32_t cfg;          // k8 | k4 << 8: smallest stride of the 8- and 4-byte windows (0: none)
+    uint32_t comb;         // index of its table (kNone if no shared pattern)
+};
+
+struct Header {
+    const GroupDesc *groups;          // ascending gstage0 (in the uploaded staging, after the jobs)
+    const uint32_t *group_jobs;      // job indices per group
+    uint32_t ngroups;
+    uint32_t njobs;
+    uint64_t gstages;       // stages over all groups (claimed in phase 1)
+    uint64_t jstages;       // stages over all patterns (emitted in phase 3)
+    uint64_t range_stages;  // pattern stages per emit range
+    uint32_t nranges;       // emit ranges (at most kRangesPerBlock x grid)
+    uint32_t pad2;
+    uint64_t capacity;
+    uint64_t *positions;
+    uint32_t emit;
+    uint32_t pad;
+};
+
+// The shared table of one group (built in global memory, copied to shared
+// memory when a block starts on the group).
+struct SharedTable {
+    uint32_t head[kSlots];           // 0, or tag << 16 | (entry + 1); tag 0: several entries
+    uint4 ent[kMaxEnt];              // {lo, hi, meta, next}; meta = i << 8 | w4 << 7 | log2 K << 4 | j
+    uint32_t pw[kMaxShared][8];      // pattern words
+    uint64_t stage0[kMaxShared];     // per-pattern stage numbering
+    uint32_t nst[kMaxShared];
+    uint32_t m[kMaxShared];
+};
+
+struct Params {
+    const Header *hdr;
+    const JobDesc *jobs;
+    SharedTable *comb;           // one per group with shared patterns
+    uint8_t *tables;             // block-variant tables of individual patterns (kTableBytes each)
+    uint64_t *offsets;           // per job: exclusive prefix at its first segment; [njobs] = total
+    uint32_t *seg_count;
+    uint16_t *seg_mask;
+    unsigned long long *range_total;  // per emit range (zeroed by the table kernel)
+    uint32_t *err;
+    DevMisc *misc;
+};
+
+constexpr int kTableBytes = kHashSlots + 16 * 4;
+
+// What a warp needs to check a candidate in full.
+struct VCtx {
+    const uint8_t *tbase;  // text base (16-byte aligned)
+    const uint8_t *buf;    // the staged stage
+    int64_t delta;         // first internal byte of the text
+    int64_t lim;           // first internal byte past the text
+    int64_t sbase;         // internal byte of buf[0]
+    uint32_t inside;       // the whole stage buffer holds text bytes
+    uint32_t pad;
+};
+
+struct alignas(128) Smem {
+    uint8_t buf[kRing][kStageBuf];
+    SharedTable tab;                             // table of the current group
+    uint64_t stage_id[kRing];
+    uint32_t stage_group[kRing];
+    uint64_t full[kRing];
+    uint64_t empty[kRing];
+    uint64_t tab_free;                           // mbarrier: every warp is done with the old table
+    uint64_t tab_ready;                          // mbarrier: every warp has copied its share
+    uint32_t hits[kConsumerWarps][kHitCap];      // pattern << 11 | chunk << 4 | bit
+    uint32_t nhits[kConsumerWarps];
+    uint16_t hitcnt[kConsumerWarps][kMaxShared];
+    uint32_t ovf[kConsumerWarps][kMaxShared / 32];  // patterns whose hits did not fit
+    VCtx vc[kConsumerWarps];
+    uint16_t emit_stage[kConsumerWarps][32 * 16];
+    uint32_t scan_tmp[kConsumerWarps];
+    uint64_t scan_tmp64[kConsumerWarps];
+    uint64_t range_excl[kRangesPerBlock];  // output offset of each range the block emits
+    uint64_t total;
+    uint64_t batch_excl[kConsumerWarps * 32];
+};
+
+// Window hashes: the head slot is the top 12 bits, the tag bits 4..19 (never 0).
+__device__ __forceinline__ uint32_t hash8(uint32_t lo, uint32_t hi) {
+    return lo * 0x9E3779B1u + hi * 0x85EBCA77u;
+}
+
+__device__ __forceinline__ uint32_t hash4(uint32_t lo) { return lo * 0x2545F491u + 0x6A09E667u; }
+
+__device__ __forceinline__ uint32_t slot_of(uint32_t x) { return x >> (32 - kSlotBits); }
+
+__device__ __forceinline__ uint32_t tag_of(uint32_t x) { return ((x >> 4) & 0xFFFFu) | 1u; }
+
+// ---------------------------------------------------------------------------
+// pattern preprocessing (a kernel): block-variant tables of individual
+// patterns and the groups' shared tables
+// ---------------------------------------------------------------------------
+
+__global__ void build_group_tables_kernel(const Params P) {
+    const Header H = *P.hdr;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < H.nranges; r += gridDim.x * blockDim.x)
+        P.range_total[r] = 0ull;
+    // block-variant tables, one block per job
+    for (uint32_t j = blockIdx.x; j < H.njobs; j += gridDim.x) {
+        const JobDesc &D = P.jobs[j];
+        if (D.table == kNone) continue;
+        uint8_t *tb = P.tables + (uint64_t)D.table * kTableBytes;
+        uint32_t *tw = reinterpret_cast<uint32_t *>(tb);
+        for (int i = threadIdx.x; i < kHashSlots / 4; i += blockDim.x) tw[i] = 0u;
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            const int q = threadIdx.x >> 2;
+            const uint32_t sh = 8u * (uint32_t)(threadIdx.x & 3);
+            const uint32_t lo = __funnelshift_r(D.job.pat.w[q], D.job.pat.w[q + 1], sh);
+            const uint32_t hi = __funnelshift_r(D.job.pat.w[q + 1], D.job.pat.w[q + 2], sh);
+            uint32_t *pb = reinterpret_cast<uint32_t *>(tb + kHashSlots);
+            pb[2 * threadIdx.x] = lo;
+            pb[2 * threadIdx.x + 1] = hi;
+            tb[block_hash(lo, hi)] = 1;
+        }
+        __syncthreads();
+    }
+    // shared tables, one block per group
+    for (uint32_t g = blockIdx.x; g < H.ngroups; g += gridDim.x) {
+        const GroupDesc &G = H.groups[g];
+        if (G.comb == kNone) continue;
+        SharedTable &T = P.comb[G.comb];
+        for (int i = threadIdx.x; i < kSlots; i += blockDim.x) T.head[i] = 0u;
+        for (uint32_t i = threadIdx.x; i < G.nshared; i += blockDim.x) {
+            const JobDesc &D = P.jobs[H.group_jobs[G.job0 + i]];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) T.pw[i][k] = D.job.pat.w[k];
+            T.stage0[i] = D.stage0;
+            T.nst[i] = (uint32_t)D.nstages;
+            T.m[i] = D.job.pat.m;
+        }
+        __syncthreads();
+        // entries: (pattern i, j) for j < K_i; insertion pushes on the slot's chain
+        for (uint32_t k = threadIdx.x; k < G.nshared * 8u; k += blockDim.x) {
+            const uint32_t i = k >> 3, j = k & 7u;
+            const JobDesc &D = P.jobs[H.group_jobs[G.job0 + i]];
+            if (j >= D.kstride) continue;
+            const Pattern &pt = D.job.pat;
+            const uint32_t q = j >> 2, sh = 8u * (j & 3u);
+            const uint32_t lo = __funnelshift_r(pt.w[q], pt.w[q + 1], sh);
+            const bool w4 = pt.m < kW8Min;
+            const uint32_t hi = w4 ? 0u : __funnelshift_r(pt.w[q + 1], pt.w[q + 2], sh);
+            const uint32_t x = w4 ? hash4(lo) : hash8(lo, hi);
+            const uint32_t lk = (uint32_t)(__ffs((int)D.kstride) - 1);
+            const uint32_t e = D.ent0 + j;
+            const uint32_t old = atomicExch(&T.head[slot_of(x)], (tag_of(x) << 16) | (e + 1u));
+            T.ent[e] = make_uint4(lo, hi, (i << 8) | ((w4 ? 1u : 0u) << 7) | (lk << 4) | j,
+                                  old ? (old & 0xFFFFu) - 1u : kEndChain);
+        }
+        __syncthreads();
+        // a slot holding a chain of several entries gets tag 0 (always walk it)
+        for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
+            const uint32_t v = T.head[i];
+            if (v && T.ent[(v & 0xFFFFu) - 1u].w != kEndChain) T.head[i] = v & 0xFFFFu;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// phase 1
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t find_group(const GroupDesc *groups, uint32_t ng, uint64_t st,
+                                               uint32_t hint) {
+    if (hint < ng && groups[hint].gstage0 <= st && st < groups[hint].gstage0 + groups[hint].nstages)
+        return hint;
+    uint32_t lo = 0, hi = ng - 1u;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1u) >> 1;
+        if (groups[mid].gstage0 <= st) lo = mid; else hi = mid - 1u;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void producer(const Params &P, const Header &H, Smem &S) {
+    uint32_t issued = 0;
+    bool failed = false;
+    uint32_t hint = 0;
+    uint64_t claim = atomicAdd(&P.misc->ticket, kClaim);
+    for (;;) {
+        if (claim >= H.gstages) {
+            const int s = issued % kRing;
+            const uint32_t n = issued / kRing;
+            if (n > 0 && !mbar_wait(&S.empty[s], (n - 1) & 1)) { failed = true; break; }
+            S.stage_id[s] = kEndStage;
+            mbar_arrive(&S.full[s]);
+            ++issued;
+            break;
+        }
+        const uint64_t next = atomicAdd(&P.misc->ticket, kClaim);
+        const uint64_t last = claim + kClaim < H.gstages ? claim + kClaim : H.gstages;
+        for (uint64_t st = claim; st < last; ++st) {
+            const int s = issued % kRing;
+            const uint32_t n = issued / kRing;
+            if (n > 0 && !mbar_wait(&S.empty[s], (n - 1) & 1)) { failed = true; break; }
+            hint = find_group(H.groups, H.ngroups, st, hint);
+            const GroupDesc &G = H.groups[hint];
+            S.stage_id[s] = st;
+            S.stage_group[s] = hint;
+            const uint64_t c0 = (st - G.gstage0) * kStageChunks;
+            const uint64_t a = c0 > G.chunk_full0 ? c0 : G.chunk_full0;
+            uint64_t b = c0 + kStageChunks + 1u;
+            if (b > G.chunk_full1) b = G.chunk_full1;
+            if (a < b) {
+                const uint32_t bytes = (uint32_t)((b - a) * 16u);
+                mbar_arrive_tx(&S.full[s], bytes);
+                bulk_load(S.buf[s] + (a - c0) * 16u, G.text.base + a * 16u, bytes, &S.full[s]);
+            } else {
+                mbar_arrive(&S.full[s]);
+            }
+            ++issued;
+        }
+        if (failed) break;
+        claim = next;
+    }
+    if (failed) atomicOr(P.err, kErrTimeout);
+    const uint32_t lo = issued > (uint32_t)kRing ? issued - kRing : 0u;
+    for (uint32_t i = lo; i < issued; ++i) mbar_wait(&S.full[i % kRing], (i / kRing) & 1);
+}
+
+// Single-search variant of one individual pattern on the staged stage, stored
+// as its segment.
+__device__ __noinline__ void plain_job(const Params &P, const Header &H, const JobDesc &D,
+                                       const uint8_t *buf, uint64_t ls, int w, int lane) {
+    const uint64_t c0 = ls * kStageChunks;
+    const BcastWords Bw(D.job.pat);
+    const uint8_t *tb = D.table == kNone ? nullptr : P.tables + (uint64_t)D.table * kTableBytes;
+    const uint32_t *pb = tb ? reinterpret_cast<const uint32_t *>(tb + kHashSlots) : nullptr;
+    const uint64_t cf0 = (D.job.delta + 15u) / 16u, cf1 = D.job.lim / 16u;
+    uint32_t h[4] = {0u, 0u, 0u, 0u};
+    uint32_t cnt;
+    switch (D.variant) {
+        case V_DIRECT: cnt = stage_hits<V_DIRECT, 0>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
+        case V_PREFIX4: cnt = stage_hits<V_PREFIX4, 4>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
+        case V_PREFIX8: cnt = stage_hits<V_PREFIX8, 8>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
+        default: cnt = stage_hits<V_BLOCK8, 8>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
+    }
+    const uint64_t st = D.stage0 + ls;
+    store_segment(P.seg_count, P.seg_mask, P.range_total, H.range_stages, st,
+                  st * kConsumerWarps + (uint64_t)w, cnt, h, H.emit != 0, lane);
+}
+
+// t[P..P+m) == p (pattern words pw), read from the staged bytes when the stage
+// buffer covers them, else from global memory.
+__device__ __forceinline__ bool verify_at(const uint32_t *pw, uint32_t m, int64_t P, const VCtx &V) {
+    const int64_t o = P - V.sbase;
+    const uint32_t nw = (m + 3u) >> 2;
+    if (V.inside && o >= 0 && o + (int64_t)m <= (int64_t)(kStageBytes + 16u)) {
+        const uint32_t *W = reinterpret_cast<const uint32_t *>(V.buf);
+        const uint32_t a = (uint32_t)o >> 2, sh = ((uint32_t)o & 3u) * 8u;
+        uint32_t cur = W[a];
+        for (uint32_t i = 0; i < nw; ++i) {
+            const uint32_t nxt = W[a + i + 1u];
+            if ((__funnelshift_r(cur, nxt, sh) ^ pw[i]) & word_mask(m, i)) return false;
+            cur = nxt;
+        }
+        return true;
+    }
+    SearchJob T;
+    T.base = V.tbase;
+    T.delta = (uint64_t)V.delta;
+    T.lim = (uint64_t)V.lim;
+    const uint64_t a = (uint64_t)P >> 2;
+    const uint32_t sh = ((uint32_t)P & 3u) * 8u;
+    uint32_t cur = load_word(T, a);
+    for (uint32_t i = 0; i < nw; ++i) {
+        const uint32_t nxt = load_word(T, a + i + 1u);
+        if ((__funnelshift_r(cur, nxt, sh) ^ pw[i]) & word_mask(m, i)) return false;
+        cur = nxt;
+    }
+    return true;
+}
+
+// Appends a confirmed hit of shared pattern i at (chunk, bit) to the warp's
+// list; a pattern whose hit does not fit is marked for the dense path.
+__device__ __forceinline__ void push_hit(Smem &S, int w, uint32_t i, uint32_t chunk, uint32_t bit) {
+    const uint32_t k = atomicAdd(&S.nhits[w], 1u);
+    if (k >= (uint32_t)kHitCap) {
+        atomicOr(&S.ovf[w][i >> 5], 1u << (i & 31u));
+        return;
+    }
+    S.hits[w][k] = (i << 11) | (chunk << 4) | bit;
+    atomicAdd(reinterpret_cast<unsigned int *>(&S.hitcnt[w][0]) + (i >> 1), (i & 1u) ? 0x10000u : 1u);
+}
+
+// Word k (0..5) of a chunk and the first two words of the next one.
+__device__ __forceinline__ uint32_t pick_word(uint4 c, uint32_t n0, uint32_t n1, uint32_t k) {
+    uint32_t r = n1;
+    r = k == 4u ? n0 : r;
+    r = k == 3u ? c.w : r;
+    r = k == 2u ? c.z : r;
+    r = k == 1u ? c.y : r;
+    r = k == 0u ? c.x : r;
+    return r;
+}
+
+// The windows whose head slot may hold them (bit q of need8 / need4 for the
+// 8- / 4-byte window at 16c + q): walk each slot's chain, compare exactly, and
+// check the matches in full.  Out of line: it runs for few lanes.
+__device__ __noinline__ void walk_chains(Smem &S, int w, uint4 cur, uint32_t n0, uint32_t n1,
+                                         uint32_t need8, uint32_t need4, int64_t p0, uint32_t chunk) {
+    const VCtx &V = S.vc[w];
+    for (uint32_t pass = 0; pass < 2; ++pass) {
+        uint32_t need = pass ? need4 : need8;
+        const uint32_t w4 = pass;
+        while (need) {
+            const uint32_t q = (uint32_t)(__ffs(need) - 1);
+            need &= need - 1u;
+            const uint32_t k = q >> 2, sh = 8u * (q & 3u);
+            const uint32_t r0 = pick_word(cur, n0, n1, k), r1 = pick_word(cur, n0, n1, k + 1u);
+            const uint32_t lo = __funnelshift_r(r0, r1, sh);
+            const uint32_t hi = w4 ? 0u : __funnelshift_r(r1, k + 2u <= 5u ? pick_word(cur, n0, n1, k + 2u) : 0u, sh);
+            const uint32_t x = w4 ? hash4(lo) : hash8(lo, hi);
+            uint32_t e = (S.tab.head[slot_of(x)] & 0xFFFFu) - 1u;
+            for (int guard = 0; guard < kMaxEnt && e < (uint32_t)kMaxEnt; ++guard) {
+                const uint4 E = S.tab.ent[e];
+                const uint32_t meta = E.z;
+                const uint32_t i = meta >> 8, j = meta & 7u, K = 1u << ((meta >> 4) & 3u);
+                if (((meta >> 7) & 1u) == w4 && E.x == lo && (w4 || E.y == hi) &&
+                    (q & (K - 1u)) == 0u && j <= q && q - j <= 15u) {
+                    const uint32_t b = q - j;
+                    const int64_t Pp = p0 + (int64_t)b;
+                    const uint32_t m = S.tab.m[i];
+                    if (Pp >= V.delta && Pp <= V.lim - (int64_t)m && verify_at(S.tab.pw[i], m, Pp, V))
+                        push_hit(S, w, i, chunk, b);
+                }
+                if (E.w == kEndChain) break;
+                e = E.w;
+            }
+        }
+    }
+}
+
+// Lookups of one chunk: 8-byte windows at q = 0, K8, 2 K8, .., 16 and 4-byte
+// windows at q = 0, K4, .., 16 (K = 0: no window of that width; every
+// stride is at least 2, so q = 16 is always looked up).  A window passes
+// when its head slot is non-empty and carries its tag or tag 0; the chains of
+// the passing windows are walked afterwards.
+template <int K8, int K4>
+__device__ __forceinline__ void filter_chunk(Smem &S, int w, uint4 cur, uint32_t n0, uint32_t n1,
+                                             int64_t p0, uint32_t chunk) {
+    const uint32_t R[6] = {cur.x, cur.y, cur.z, cur.w, n0, n1};
+    const uint32_t *head = S.tab.head;
+    uint32_t need8 = 0u, need4 = 0u;
+#pragma unroll
+    for (int q = 0; q <= 16; ++q) {
+        const int k = q >> 2, j = q & 3;
+        const uint32_t lo = j ? __funnelshift_r(R[k], R[k + 1], 8 * j) : R[k];
+        if constexpr (K8 != 0) {
+            if (q % K8 == 0) {
+                const uint32_t hi = q == 16 ? R[5] : (j ? __funnelshift_r(R[k + 1], R[k + 2 < 6 ? k + 2 : 5], 8 * j) : R[k + 1]);
+                const uint32_t x = hash8(lo, hi);
+                const uint32_t v = head[slot_of(x)];
+                const uint32_t t = v >> 16;
+                if (v && (t == tag_of(x) || t == 0u)) need8 |= 1u << q;
+            }
+        }
+        if constexpr (K4 != 0) {
+            if (q % K4 == 0) {
+                const uint32_t x = hash4(lo);
+                const uint32_t v = head[slot_of(x)];
+                const uint32_t t = v >> 16;
+                if (v && (t == tag_of(x) || t == 0u)) need4 |= 1u << q;
+            }
+        }
+    }
+    if (need8 | need4) walk_chains(S, w, cur, n0, n1, need8, need4, p0, chunk);
+}
+
+// Dense path: shared pattern i alone on the warp's segment, with its prefix
+// (4 or 8 bytes) compared at every start and candidates checked in full.
+__device__ __noinline__ void pattern_pass(const Params &P, const Header &H, const GroupDesc &G,
+                                          Smem &S, uint32_t i, uint64_t ls, int w, int lane) {
+    const VCtx &V = S.vc[w];
+    const uint32_t *pw = S.tab.pw[i];
+    const uint32_t m = S.tab.m[i];
+    const uint64_t c0 = ls * kStageChunks;
+    uint4 ch[4];
+    uint4 halo;
+    load_segment(G.text, G.chunk_full0, G.chunk_full1, V.buf, c0, w, lane, true, ch, halo);
+    uint32_t b[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) b[k] = bcast_byte(pw[k >> 2], k & 3);
+    const int64_t sp0 = (int64_t)((c0 + (uint64_t)w * kSegChunks) * 16u);
+    const int64_t pmax = V.lim - (int64_t)m;
+    const int src = (lane + 1) & 31;
+    uint32_t h[4];
+    uint32_t cnt = 0u;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const uint4 cur = ch[u];
+        const uint4 nsrc = (lane == 0) ? (u + 1 < 4 ? ch[u + 1 < 4 ? u + 1 : u] : halo) : cur;
+        const uint32_t n0 = __shfl_sync(kFull, nsrc.x, src);
+        const uint32_t n1 = __shfl_sync(kFull, nsrc.y, src);
+        const uint32_t R[6] = {cur.x, cur.y, cur.z, cur.w, n0, n1};
+        uint32_t cand = 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t X = window_mismatch<4>(0u, R[k], R[k + 1], b[0], b[1], b[2], b[3]);
+            if (m >= 8u) X = window_mismatch<4>(X, R[k + 1], R[k + 2], b[4], b[5], b[6], b[7]);
+            cand |= nibble_of(zero_bytes(X)) << (4 * k);
+        }
+        const int64_t p0 = sp0 + (int64_t)((32 * u + lane) * 16);
+        cand &= range_mask(V.delta - p0, pmax - p0);
+        uint32_t hh = 0u;
+        while (cand) {
+            const int bit = __ffs(cand) - 1;
+            cand &= cand - 1u;
+            if (verify_at(pw, m, p0 + bit, V)) hh |= 1u << bit;
+        }
+        h[u] = hh;
+        cnt += __popc(hh);
+    }
+    const uint64_t st = S.tab.stage0[i] + ls;
+    store_segment(P.seg_count, P.seg_mask, P.range_total, H.range_stages, st,
+                  st * kConsumerWarps + (uint64_t)w, cnt, h, H.emit != 0, lane);
+}
+
+// Writes the segment of every shared pattern: count 0 for patterns without
+// hits, masks from the hit list for the others, the dense path for patterns
+// whose hits did not fit.
+__device__ __forceinline__ void finish_shared(const Params &P, const Header &H, const GroupDesc &G,
+                                              Smem &S, uint64_t ls, int w, int lane) {
+    const uint32_t nS = G.nshared;
+    const uint32_t nh = S.nhits[w] < (uint32_t)kHitCap ? S.nhits[w] : (uint32_t)kHitCap;
+    uint32_t *mbuf = reinterpret_cast<uint32_t *>(S.emit_stage[w]);  // 128 chunk masks
+    for (uint32_t i0 = 0; i0 < nS; i0 += 32) {
+        const uint32_t i = i0 + (uint32_t)lane;
+        const bool valid = i < nS && ls < S.tab.nst[i < nS ? i : 0];
+        const bool over = valid && ((S.ovf[w][i >> 5] >> (i & 31u)) & 1u);
+        const uint32_t hc = valid ? S.hitcnt[w][i] : 0u;
+        if (valid && !over && hc == 0u)
+            P.seg_count[(S.tab.stage0[i] + ls) * kConsumerWarps + (uint64_t)w] = 0u;
+        uint32_t todo = __ballot_sync(kFull, valid && !over && hc != 0u);
+        while (todo) {
+            const uint32_t ii = i0 + (uint32_t)(__ffs(todo) - 1);
+            todo &= todo - 1u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) mbuf[u * 32 + lane] = 0u;
+            __syncwarp();
+            for (uint32_t k = lane; k < nh; k += 32) {
+                const uint32_t e = S.hits[w][k];
+                if ((e >> 11) == ii) atomicOr(&mbuf[(e >> 4) & 127u], 1u << (e & 15u));
+            }
+            __syncwarp();
+            uint32_t h[4];
+            uint32_t cnt = 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                h[u] = mbuf[u * 32 + lane];
+                cnt += __popc(h[u]);
+            }
+            __syncwarp();
+            const uint64_t st = S.tab.stage0[ii] + ls;
+            store_segment(P.seg_count, P.seg_mask, P.range_total, H.range_stages, st,
+                          st * kConsumerWarps + (uint64_t)w, cnt, h, H.emit != 0, lane);
+        }
+        uint32_t dense = __ballot_sync(kFull, over);
+        while (dense) {
+            const uint32_t ii = i0 + (uint32_t)(__ffs(dense) - 1);
+            dense &= dense - 1u;
+            pattern_pass(P, H, G, S, ii, ls, w, lane);
+        }
+    }
+}
+
+// Shared filter of one group on one staged stage (a whole consumer warp).
+template <int K8, int K4>
+__device__ __noinline__ void shared_filter(const Params &P, const Header &H, const GroupDesc &G,
+                                           Smem &S, const uint8_t *buf, uint64_t ls, int w, int lane) {
+    const uint64_t c0 = ls * kStageChunks;
+    if (lane == 0) {
+        S.nhits[w] = 0u;
+        VCtx &V = S.vc[w];
+        V.tbase = G.text.base;
+        V.buf = buf;
+        V.delta = (int64_t)G.text.delta;
+        V.lim = (int64_t)G.text.lim;
+        V.sbase = (int64_t)(c0 * 16u);
+        V.inside = (c0 >= G.chunk_full0 && c0 + kStageChunks + 1u <= G.chunk_full1) ? 1u : 0u;
+    }
+    if (lane < kMaxShared / 32) S.ovf[w][lane] = 0u;
+    for (uint32_t i = lane; i < (G.nshared + 1u) / 2u; i += 32)
+        reinterpret_cast<uint32_t *>(&S.hitcnt[w][0])[i] = 0u;
+    __syncwarp();
+    uint4 ch[4];
+    uint4 halo;
+    load_segment(G.text, G.chunk_full0, G.chunk_full1, buf, c0, w, lane, true, ch, halo);
+    const int64_t sp0 = (int64_t)((c0 + (uint64_t)w * kSegChunks) * 16u);
+    const int src = (lane + 1) & 31;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const uint4 cur = ch[u];
+        const uint4 nsrc = (lane == 0) ? (u + 1 < 4 ? ch[u + 1 < 4 ? u + 1 : u] : halo) : cur;
+        const uint32_t n0 = __shfl_sync(kFull, nsrc.x, src);
+        const uint32_t n1 = __shfl_sync(kFull, nsrc.y, src);
+        filter_chunk<K8, K4>(S, w, cur, n0, n1, sp0 + (int64_t)((32 * u + lane) * 16),
+                             (uint32_t)(32 * u + lane));
+    }
+    __syncwarp();
+    finish_shared(P, H, G, S, ls, w, lane);
+}
+
+// Shared filter dispatch on the group's smallest strides.
+__device__ __forceinline__ void shared_filter_any(const Params &P, const Header &H, const GroupDesc &G,
+                                                  Smem &S, const uint8_t *buf, uint64_t ls, int w,
+                                                  int lane) {
+    const uint32_t k8 = G.cfg & 0xFFu, k4 = (G.cfg >> 8) & 0xFFu;
+    switch (k8 * 16u + k4) {
+        case 0x02: shared_filter<0, 2>(P, H, G, S, buf, ls, w, lane); break;
+        case 0x04: shared_filter<0, 4>(P, H, G, S, buf, ls, w, lane); break;
+        case 0x40: shared_filter<4, 0>(P, H, G, S, buf, ls, w, lane); break;
+        case 0x42: shared_filter<4, 2>(P, H, G, S, buf, ls, w, lane); break;
+        case 0x44: shared_filter<4, 4>(P, H, G, S, buf, ls, w, lane); break;
+        case 0x80: shared_filter<8, 0>(P, H, G, S, buf, ls, w, lane); break;
+        case 0x82: shared_filter<8, 2>(P, H, G, S, buf, ls, w, lane); break;
+        default: shared_filter<8, 4>(P, H, G, S, buf, ls, w, lane); break;
+    }
+}
+
+// The group's short patterns (m <= 4) on one staged stage: the packed window
+// compare of Section 3.2 for each of them on the segment loaded once.
+__device__ __noinline__ void direct_jobs(const Params &P, const Header &H, const GroupDesc &G,
+                                         const uint8_t *buf, uint64_t ls, int w, int lane) {
+    const uint64_t c0 = ls * kStageChunks;
+    uint4 ch[4];
+    uint4 halo;
+    load_segment(G.text, G.chunk_full0, G.chunk_full1, buf, c0, w, lane, true, ch, halo);
+    const int src = (lane + 1) & 31;
+    uint32_t nx[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const uint4 nsrc = (lane == 0) ? (u + 1 < 4 ? ch[u + 1 < 4 ? u + 1 : u] : halo) : ch[u];
+        nx[u] = __shfl_sync(kFull, nsrc.x, src);
+    }
+    const int64_t sp0 = (int64_t)((c0 + (uint64_t)w * kSegChunks) * 16u);
+    const int64_t delta = (int64_t)G.text.delta;
+    for (uint32_t i = 0; i < G.nindiv; ++i) {
+        const JobDesc &D = P.jobs[H.group_jobs[G.job0 + G.nshared + i]];
+        if (ls >= D.nstages) continue;
+        const uint32_t m = D.job.pat.m, p0w = D.job.pat.w[0];
+        const uint32_t b0 = bcast_byte(p0w, 0), b1 = bcast_byte(p0w, 1);
+        const uint32_t b2 = bcast_byte(p0w, 2), b3 = bcast_byte(p0w, 3);
+        const uint32_t mk1 = m <= 1u ? 0u : 0xFFFFFFFFu, mk2 = m <= 2u ? 0u : 0xFFFFFFFFu;
+        const uint32_t mk3 = m <= 3u ? 0u : 0xFFFFFFFFu;
+        const int64_t pmax = D.job.pmax;
+        const bool interior = sp0 >= delta && sp0 + (int64_t)(kSegChunks * 16) - 1 <= pmax;
+        uint32_t h[4];
+        uint32_t cnt = 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t R[5] = {ch[u].x, ch[u].y, ch[u].z, ch[u].w, nx[u]};
+            uint32_t hh = 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t X = (R[k] ^ b0) | ((__funnelshift_r(R[k], R[k + 1], 8) ^ b1) & mk1) |
+                                   ((__funnelshift_r(R[k], R[k + 1], 16) ^ b2) & mk2) |
+                                   ((__funnelshift_r(R[k], R[k + 1], 24) ^ b3) & mk3);
+                hh |= nibble_of(zero_bytes(X)) << (4 * k);
+            }
+            if (!interior) {
+                const int64_t p0 = sp0 + (int64_t)((32 * u + lane) * 16);
+                hh &= range_mask(delta - p0, pmax - p0);
+            }
+            h[u] = hh;
+            cnt += __popc(hh);
+        }
+        const uint64_t st = D.stage0 + ls;
+        store_segment(P.seg_count, P.seg_mask, P.range_total, H.range_stages, st,
+                      st * kConsumerWarps + (uint64_t)w, cnt, h, H.emit != 0, lane);
+    }
+}
+
+__device__ __forceinline__ void consumer(const Params &P, const Header &H, Smem &S, int w, int lane,
+                                         bool *ok) {
+    int s = 0;
+    uint32_t phase = 0;
+    const int t = w * 32 + lane;
+    uint32_t tab_group = kNone;  // group whose table this warp last loaded
+    uint32_t tab_loads = 0;      // table loads so far (mbarrier phase parity)
+    for (;;) {
+        if (!warp_wait(&S.full[s], phase)) { *ok = false; break; }
+        const uint64_t st = S.stage_id[s];
+        if (st == kEndStage) break;
+        const uint32_t g = S.stage_group[s];
+        const GroupDesc &G = H.groups[g];
+        const uint64_t ls = st - G.gstage0;
+        const uint8_t *buf = S.buf[s];
+        // load the group's table: every consumer warp reaches this stage;
+        // bounded mbarrier waits (not a block barrier) so that a warp that
+        // gave up cannot hold the others forever
+        if (G.comb != kNone && tab_group != g) {
+            if (lane == 0) mbar_arrive(&S.tab_free);
+            if (!warp_wait(&S.tab_free, tab_loads & 1u)) { *ok = false; break; }
+            const uint4 *src = reinterpret_cast<const uint4 *>(&P.comb[G.comb]);
+            uint4 *dst = reinterpret_cast<uint4 *>(&S.tab);
+            for (int i = t; i < (int)(sizeof(SharedTable) / 16); i += kConsumerWarps * 32) dst[i] = src[i];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.tab_ready);
+            if (!warp_wait(&S.tab_ready, tab_loads & 1u)) { *ok = false; break; }
+            ++tab_loads;
+            tab_group = g;
+        }
+        // individual patterns: a pattern alone on its text runs its own
+        // variant; the short patterns of a shared text run together
+        if (G.nindiv == 1u && G.nshared == 0u) {
+            const JobDesc &D = P.jobs[H.group_jobs[G.job0]];
+            if (ls < D.nstages) plain_job(P, H, D, buf, ls, w, lane);
+        } else if (G.nindiv) {
+            direct_jobs(P, H, G, buf, ls, w, lane);
+        }
+        if (G.nshared) shared_filter_any(P, H, G, S, buf, ls, w, lane);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.empty[s]);
+        if (++s == kRing) { s = 0; phase ^= 1u; }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// phase 3 (per-pattern segment numbering, as the plain batched launch)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t first_job_from(const JobDesc *jobs, uint32_t njobs, uint64_t st) {
+    uint32_t lo = 0, hi = njobs;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (jobs[mid].stage0 < st) lo = mid + 1u; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void emit_range(const Params &P, const Header &H, Smem &S, uint64_t st0,
+                                           uint64_t st1, uint64_t cta_excl, int w, int lane) {
+    const int t = w * 32 + lane;
+    const uint64_t seg0 = st0 * kConsumerWarps, seg1 = st1 * kConsumerWarps;
+    uint64_t base = cta_excl;
+    uint32_t jcur = first_job_from(P.jobs, H.njobs, st0);
+    uint32_t wj = jcur > 0 ? jcur - 1u : 0u;
+    for (uint64_t sb = seg0; sb < seg1; sb += kConsumerWarps * 32) {
+        const uint64_t seg = sb + (uint64_t)t;
+        const uint32_t c = seg < seg1 ? P.seg_count[seg] : 0u;
+        const uint32_t inc = warp_incl_scan(c, lane);
+        if (lane == 31) S.scan_tmp[w] = inc;
+        consumer_sync();
+        uint32_t wbase = 0u, btotal = 0u;
+#pragma unroll
+        for (int k = 0; k < kConsumerWarps; ++k) {
+            const uint32_t v = S.scan_tmp[k];
+            if (k < w) wbase += v;
+            btotal += v;
+        }
+        const uint64_t excl = base + wbase + inc - c;
+        S.batch_excl[t] = excl;
+        consumer_sync();
+        if (t == 0) {
+            const uint64_t bst1 = (sb + kConsumerWarps * 32) / kConsumerWarps;
+            while (jcur < H.njobs && P.jobs[jcur].stage0 < bst1 && P.jobs[jcur].stage0 < st1) {
+                P.offsets[jcur] = S.batch_excl[P.jobs[jcur].stage0 * kConsumerWarps - sb];
+                ++jcur;
+            }
+        }
+        const uint32_t todo = __ballot_sync(kFull, c != 0u);
+        if (todo && H.emit) {
+            emit_list(todo, sb + (uint64_t)w * 32u, excl, P.seg_mask, lane,
+                      [&](uint64_t sj, uint64_t ej, uint2 packed) {
+                          const uint64_t stg = sj / kConsumerWarps;
+                          while (wj + 1u < H.njobs && P.jobs[wj + 1u].stage0 <= stg) ++wj;
+                          const JobDesc &D = P.jobs[wj];
+                          const int64_t s0 = (int64_t)(((stg - D.stage0) * kStageChunks +
+                                                        (sj % kConsumerWarps) * kSegChunks) * 16u) +
+                                             D.off - (int64_t)D.job.delta;
+                          emit_segment(H.positions, H.capacity, P.err, s0, ej, packed,
+                                       S.emit_stage[w], lane);
+                      });
+        }
+        base += btotal;
+        consumer_sync();
+    }
+}
+
+}  // namespace group
+
+__global__ void __launch_bounds__(stream::kThreadsStream, stream::kMaxBlocksPerSm)
+    group_kernel(const __grid_constant__ group::Params P) {
+    using namespace group;
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    const Header H = *P.hdr;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kRing; ++s) {
+            mbar_init(&S.full[s], 1);
+            mbar_init(&S.empty[s], kConsumerWarps);
+        }
+        mbar_init(&S.tab_free, kConsumerWarps);
+        mbar_init(&S.tab_ready, kConsumerWarps);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    bool ok = true;
+    if (H.ngroups > 0) {
+        if (warp == kConsumerWarps) {
+            if (lane == 0) producer(P, H, S);
+        } else {
+            consumer(P, H, S, warp, lane, &ok);
+            if (!ok && lane == 0) atomicOr(P.err, kErrTimeout);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !grid_barrier(P.misc)) atomicOr(P.err, kErrTimeout);
+    __syncthreads();
+
+    // phase 2: block b emits ranges b, b + grid, b + 2 grid, ...  Each block
+    // takes the exclusive prefix of all range totals: consumer thread t sums a
+    // slice of them, one block scan over the slices, and the owner of a slice
+    // holding one of the block's ranges adds the slice's part before it.
+    const uint32_t nr = H.nranges, G = gridDim.x, b = blockIdx.x;
+    if (warp < kConsumerWarps) {
+        const int t = warp * 32 + lane;
+        const uint32_t per = (nr + kConsumerWarps * 32 - 1) / (kConsumerWarps * 32);
+        const uint32_t r0 = (uint32_t)t * per, r1 = r0 + per < nr ? r0 + per : nr;
+        const uint64_t *rt = reinterpret_cast<const uint64_t *>(P.range_total);
+        uint64_t sum = 0;
+        for (uint32_t r = r0; r < r1; ++r) sum += ld_relaxed_u64(rt + r);
+        uint64_t inc = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint64_t v = __shfl_up_sync(kFull, inc, d);
+            if (lane >= d) inc += v;
+        }
+        if (lane == 31) S.scan_tmp64[warp] = inc;
+        consumer_sync();
+        uint64_t before = 0, all = 0;
+#pragma unroll
+        for (int k = 0; k < kConsumerWarps; ++k) {
+            const uint64_t v = S.scan_tmp64[k];
+            if (k < warp) before += v;
+            all += v;
+        }
+        uint64_t run = before + inc - sum;
+        for (uint32_t r = r0; r < r1; ++r) {
+            if (r % G == b) S.range_excl[r / G] = run;
+            run += ld_relaxed_u64(rt + r);
+        }
+        if (t == 0) {
+            S.total = all;
+            if (b == 0) P.offsets[H.njobs] = all;
+        }
+    }
+    __syncthreads();
+    // phase 3
+    if (warp < kConsumerWarps && H.njobs > 0) {
+        for (uint32_t r = b, k = 0; r < nr; r += G, ++k) {
+            const uint64_t st0 = (uint64_t)r * H.range_stages;
+            const uint64_t st1 = st0 + H.range_stages < H.jstages ? st0 + H.range_stages : H.jstages;
+            if (st0 < st1) emit_range(P, H, S, st0, st1, S.range_excl[k], warp, lane);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t d = atomicAdd(&P.misc->done, 1u);
+        if (d == gridDim.x - 1u) {
+            P.misc->ticket = 0u;
+            P.misc->done = 0u;
+            P.misc->barrier = 0u;
+            __threadfence();
+        }
+    }
+}
+
+}  // namespace epsm

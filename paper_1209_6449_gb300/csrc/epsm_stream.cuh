@@ -220,6 +220,29 @@ __device__ __noinline__ uint4 edge_chunk(const SearchJob &J, uint64_t cf0, uint6
     return staged_chunk(J, cf0, cf1, buf, c0, c);
 }
 
+// The four chunks lane l holds for segment w of a staged stage (chunks 32u + l
+// of the segment), and for lane 0 the halo chunk after the segment.
+__device__ __forceinline__ void load_segment(const SearchJob &J, uint64_t cf0, uint64_t cf1,
+                                             const uint8_t *buf, uint64_t c0, int w, int lane,
+                                             bool want_halo, uint4 (&ch)[4], uint4 &halo) {
+    const uint32_t lane_off = (uint32_t)(w * kSegChunks + lane) * 16u;  // byte offset in a stage
+    // stage entirely inside the text (all but the first and last stages):
+    // 32-bit shared-memory offsets, no per-chunk bounds checks
+    const bool inside = c0 >= cf0 && c0 + kStageChunks + 1u <= cf1;
+    halo = make_uint4(0u, 0u, 0u, 0u);
+    if (inside) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            ch[u] = *reinterpret_cast<const uint4 *>(buf + lane_off + 512u * u);
+        if (want_halo && lane == 0) halo = *reinterpret_cast<const uint4 *>(buf + lane_off + 2048u);
+    } else {
+        const uint64_t cw = c0 + (uint64_t)w * kSegChunks;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ch[u] = edge_chunk(J, cf0, cf1, buf, c0, cw + 32u * u + lane);
+        if (want_halo && lane == 0) halo = edge_chunk(J, cf0, cf1, buf, c0, cw + kSegChunks);
+    }
+}
+
 // Filter and verify one consumer warp's segment of a staged stage of job J:
 // the stage holds the job's chunks c0 .. c0+1024 (+ halo); lane l takes chunks
 // 32u + l of segment w.  Writes the four 16-bit hit masks to h and returns the
@@ -230,23 +253,9 @@ __device__ __forceinline__ uint32_t stage_hits(const SearchJob &J, uint64_t cf0,
                                                const uint32_t *pblk, const uint8_t *buf,
                                                uint64_t c0, int w, int lane, uint32_t (&h)[4]) {
     constexpr int OFF = (V == V_BLOCK8) ? -7 : 0;
-    const uint32_t lane_off = (uint32_t)(w * kSegChunks + lane) * 16u;  // byte offset in a stage
-    // stage entirely inside the text (all but the first and last stages):
-    // 32-bit shared-memory offsets, no per-chunk bounds checks
-    const bool inside = c0 >= cf0 && c0 + kStageChunks + 1u <= cf1;
     uint4 ch[4];
-    uint4 halo = make_uint4(0u, 0u, 0u, 0u);
-    if (inside) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            ch[u] = *reinterpret_cast<const uint4 *>(buf + lane_off + 512u * u);
-        if (V != V_BLOCK8 && lane == 0) halo = *reinterpret_cast<const uint4 *>(buf + lane_off + 2048u);
-    } else {
-        const uint64_t cw = c0 + (uint64_t)w * kSegChunks;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) ch[u] = edge_chunk(J, cf0, cf1, buf, c0, cw + 32u * u + lane);
-        if (V != V_BLOCK8 && lane == 0) halo = edge_chunk(J, cf0, cf1, buf, c0, cw + kSegChunks);
-    }
+    uint4 halo;
+    load_segment(J, cf0, cf1, buf, c0, w, lane, V != V_BLOCK8, ch, halo);
     const int64_t sp0 = (int64_t)((c0 + (uint64_t)w * kSegChunks) * 16u) + OFF;
     const bool interior = sp0 >= (int64_t)J.delta && sp0 + (int64_t)(kSegChunks * 16) - 1 <= J.pmax;
     uint32_t cnt = 0u;

@@ -128,12 +128,24 @@ __device__ __forceinline__ uint32_t chunk_hits(const SearchJob &J, const uint4 c
     if constexpr (V == V_DIRECT) {
         // Section 3.2 (EPSMa): every start is compared against the whole
         // (m <= 4) pattern at once; no verify step.
+        // MP = 0: m read at run time (one code path for m = 1..4); the
+        // compares of bytes at or past m are masked off.
         uint32_t n0 = __shfl_sync(kFull, nsrc.x, src);
         uint32_t R[5] = {cur.x, cur.y, cur.z, cur.w, n0};
         uint32_t h = 0u;
+        const uint32_t mk1 = (MP == 0 && pat.m <= 1u) ? 0u : 0xFFFFFFFFu;
+        const uint32_t mk2 = (MP == 0 && pat.m <= 2u) ? 0u : 0xFFFFFFFFu;
+        const uint32_t mk3 = (MP == 0 && pat.m <= 3u) ? 0u : 0xFFFFFFFFu;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            uint32_t X = window_mismatch<MP>(0u, R[k], R[k + 1], B.b[0], B.b[1], B.b[2], B.b[3]);
+            uint32_t X;
+            if constexpr (MP == 0) {
+                X = (R[k] ^ B.b[0]) | ((__funnelshift_r(R[k], R[k + 1], 8) ^ B.b[1]) & mk1) |
+                    ((__funnelshift_r(R[k], R[k + 1], 16) ^ B.b[2]) & mk2) |
+                    ((__funnelshift_r(R[k], R[k + 1], 24) ^ B.b[3]) & mk3);
+            } else {
+                X = window_mismatch<MP>(0u, R[k], R[k + 1], B.b[0], B.b[1], B.b[2], B.b[3]);
+            }
             h |= nibble_of(zero_bytes(X)) << (4 * k);
         }
         return h;
