@@ -18,13 +18,15 @@ from . import _native
 from ._native import (MAX_M, STATIC_MAX_TEXT, STATUS_NAMES, VARIANT_AUTO, VARIANT_BLOCK8, VARIANT_DIRECT,
                       VARIANT_NAMES, VARIANT_PREFIX4, VARIANT_PREFIX8)
 
-__all__ = ["Context", "EpsmError", "epsm_create", "epsm_destroy", "epsm_status_str",
+__all__ = ["Context", "EpsmError", "Server", "epsm_create", "epsm_destroy", "epsm_status_str",
            "epsm_search", "epsm_search_async", "epsm_search_variant", "epsm_sync",
            "epsm_search_batch", "epsm_search_host", "epsm_variant_for", "epsm_set_variant",
            "epsm_launch_count", "epsm_search_static", "STATIC_MAX_TEXT", "MAX_M", "VARIANT_AUTO", "VARIANT_DIRECT", "VARIANT_PREFIX4",
            "VARIANT_PREFIX8", "VARIANT_BLOCK8", "VARIANT_NAMES"]
 
 _lib = _native.load()
+
+from .serve import Server  # noqa: E402  (needs the loaded library)
 
 
 class EpsmError(RuntimeError):
@@ -84,19 +86,30 @@ def epsm_sync(ctx: int, stream: int = 0) -> int:
     return _lib.epsm_sync(ctx, stream)
 
 
+def _pattern_table(patterns: Sequence[bytes]):
+    """One buffer holding all patterns and the array of their addresses."""
+    blob = b"".join(patterns)
+    buf = np.frombuffer(blob, dtype=np.uint8) if blob else np.zeros(1, dtype=np.uint8)
+    ms = np.fromiter((len(p) for p in patterns), dtype=np.uint32, count=len(patterns))
+    starts = np.zeros(len(patterns), dtype=np.uint64)
+    if len(patterns) > 1:
+        np.cumsum(ms[:-1], dtype=np.uint64, out=starts[1:])
+    ptrs = starts + np.uint64(buf.ctypes.data)
+    return buf, ptrs, ms
+
+
 def epsm_search_batch(ctx: int, texts: Sequence[int], ns: Sequence[int],
                       patterns: Sequence[bytes], positions: int, capacity: int,
                       stream: int = 0):
     """Returns (status, offsets ndarray[npairs+1])."""
-    npairs = len(texts)
-    t_arr = (ctypes.c_void_p * max(npairs, 1))(*texts)
+    npairs = len(patterns)
+    t_arr = np.ascontiguousarray(texts, dtype=np.uint64)
     n_arr = np.ascontiguousarray(ns, dtype=np.uint64)
-    keep = [ctypes.create_string_buffer(p, len(p)) for p in patterns]
-    p_arr = (ctypes.c_void_p * max(npairs, 1))(*[ctypes.addressof(k) for k in keep])
-    m_arr = np.ascontiguousarray([len(p) for p in patterns], dtype=np.uint32)
+    keep, p_arr, m_arr = _pattern_table(patterns)
     offs = np.zeros(npairs + 1, dtype=np.uint64)
-    st = _lib.epsm_search_batch(ctx, npairs, t_arr, n_arr.ctypes.data, p_arr, m_arr.ctypes.data,
-                                positions, capacity, offs.ctypes.data, stream)
+    st = _lib.epsm_search_batch(ctx, npairs, t_arr.ctypes.data, n_arr.ctypes.data, p_arr.ctypes.data,
+                                m_arr.ctypes.data, positions, capacity, offs.ctypes.data, stream)
+    del keep
     return st, offs
 
 
@@ -235,14 +248,8 @@ class Context:
         """Batched search.  ``texts`` are uint8 CUDA tensors (or (ptr, n) tuples).
         Returns (offsets ndarray[npairs+1], positions int64 CUDA tensor)."""
         torch = self._torch
-        ptrs, ns = [], []
-        for t in texts:
-            if isinstance(t, tuple):
-                ptrs.append(t[0])
-                ns.append(t[1])
-            else:
-                ptrs.append(t.data_ptr() if t.numel() else 0)
-                ns.append(t.numel())
+        ptrs = [t[0] if isinstance(t, tuple) else (t.data_ptr() if t.numel() else 0) for t in texts]
+        ns = [t[1] if isinstance(t, tuple) else t.numel() for t in texts]
         out = torch.empty(max(capacity, 1), dtype=torch.int64, device=f"cuda:{self.device}")
         st, offs = epsm_search_batch(self.handle, ptrs, ns, patterns,
                                      out.data_ptr() if capacity else 0, capacity,

@@ -21,7 +21,10 @@ MAX_M = 32
 EXPORTS = ["epsm_create", "epsm_destroy", "epsm_status_str", "epsm_last_error",
            "epsm_search", "epsm_search_async", "epsm_search_variant", "epsm_sync",
            "epsm_search_batch", "epsm_search_host", "epsm_variant_for", "epsm_set_variant",
-           "epsm_launch_count", "epsm_search_static", "epsm_batch_uses_graph"]
+           "epsm_launch_count", "epsm_search_static", "epsm_batch_uses_graph",
+           "epsm_server_create", "epsm_server_destroy", "epsm_server_add_corpus",
+           "epsm_server_upload", "epsm_server_submit", "epsm_server_poll", "epsm_server_read",
+           "epsm_server_release", "epsm_server_replay", "epsm_server_stats_get"]
 STATIC_MAX_TEXT = 64 << 20
 
 
@@ -72,6 +75,27 @@ def load(path: str | None = None):
     lib.epsm_batch_uses_graph.restype = i32
     lib.epsm_search_static.argtypes = [vp, u64, vp, u32, vp, u64, vp, vp]
     lib.epsm_search_static.restype = st
+    i64 = ctypes.c_int64
+    lib.epsm_server_create.argtypes = [ctypes.POINTER(vp), i32, vp]
+    lib.epsm_server_create.restype = st
+    lib.epsm_server_destroy.argtypes = [vp]
+    lib.epsm_server_destroy.restype = st
+    lib.epsm_server_add_corpus.argtypes = [vp, vp, u64, ctypes.POINTER(u32)]
+    lib.epsm_server_add_corpus.restype = st
+    lib.epsm_server_upload.argtypes = [vp, vp, u64, ctypes.POINTER(u64)]
+    lib.epsm_server_upload.restype = st
+    lib.epsm_server_submit.argtypes = [vp, u32, vp, u32, ctypes.POINTER(u64)]
+    lib.epsm_server_submit.restype = st
+    lib.epsm_server_poll.argtypes = [vp, vp, u32, i64]
+    lib.epsm_server_poll.restype = u32
+    lib.epsm_server_read.argtypes = [vp, u64, vp, u64]
+    lib.epsm_server_read.restype = st
+    lib.epsm_server_release.argtypes = [vp, u64]
+    lib.epsm_server_release.restype = st
+    lib.epsm_server_replay.argtypes = [vp, u32, vp, vp, vp, vp, vp]
+    lib.epsm_server_replay.restype = st
+    lib.epsm_server_stats_get.argtypes = [vp, vp]
+    lib.epsm_server_stats_get.restype = st
     if path is None:
         _lib = lib
     return lib

@@ -14,8 +14,6 @@
 
 #include <algorithm>
 #include <mutex>
-#include <map>
-#include <utility>
 #include <vector>
 
 #include "epsm.h"
@@ -90,7 +88,19 @@ struct BatchRes {
     cudaGraph_t graph = nullptr;     // kept: its node handles address the exec's copies
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t up = nullptr, down = nullptr;
-    uint64_t graph_seg_cap = 0;      // scratch size the graph was built with
+    uint32_t *seg_count = nullptr;   // per pattern segment: hits
+    uint32_t *seg_off = nullptr;     // per pattern segment: hit list in pool
+    uint64_t seg_cap = 0;
+    uint16_t *pool = nullptr;        // hit lists
+    uint64_t pool_alloc = 0;
+    uint32_t *pool_ctr = nullptr;
+    // the submitted batch, for batch_complete
+    std::vector<int32_t> pend_jidx;  // pair -> job (-1: no stages)
+    uint32_t pend_npairs = 0;
+    uint32_t pend_nj = 0;
+    uint64_t pend_capacity = 0;
+    uint64_t gen = 1;                // bumped when a buffer the graph uses moves
+    uint64_t graph_gen = 0;          // generation the graph was built with
     bool graph_failed = false;       // a build failed once: launch directly
     int grid = 0;
 };
@@ -302,6 +312,10 @@ void free_batch(BatchRes &R) {
     if (R.tables) cudaFree(R.tables);
     if (R.comb) cudaFree(R.comb);
     if (R.rt) cudaFree(R.rt);
+    if (R.seg_count) cudaFree(R.seg_count);
+    if (R.seg_off) cudaFree(R.seg_off);
+    if (R.pool) cudaFree(R.pool);
+    if (R.pool_ctr) cudaFree(R.pool_ctr);
     R = BatchRes();
 }
 
@@ -367,6 +381,39 @@ epsm_status ensure_batch(epsm_ctx *c, uint32_t njobs, uint32_t ncomb, cudaStream
     return EPSM_OK;
 }
 
+// Per-segment counts and list offsets for nseg pattern segments, and a hit
+// list pool of pool_need entries (grown, never shrunk).
+epsm_status ensure_batch_scratch(epsm_ctx *c, uint64_t nseg, uint64_t pool_need, cudaStream_t s) {
+    BatchRes &R = c->batch;
+    if (nseg > R.seg_cap) {
+        const uint64_t cap = std::max<uint64_t>(nseg, R.seg_cap * 2);
+        CK(cudaStreamSynchronize(s));
+        if (R.seg_count) CK(cudaFree(R.seg_count));
+        if (R.seg_off) CK(cudaFree(R.seg_off));
+        R.seg_count = R.seg_off = nullptr;
+        R.seg_cap = 0;
+        CK(cudaMalloc((void **)&R.seg_count, cap * sizeof(uint32_t)));
+        CK(cudaMalloc((void **)&R.seg_off, cap * sizeof(uint32_t)));
+        R.seg_cap = cap;
+        ++R.gen;
+    }
+    if (!R.pool_ctr) {
+        CK(cudaMalloc((void **)&R.pool_ctr, sizeof(uint32_t)));
+        ++R.gen;
+    }
+    if (pool_need > R.pool_alloc) {
+        const uint64_t cap = std::max<uint64_t>(pool_need, R.pool_alloc + R.pool_alloc / 2);
+        CK(cudaStreamSynchronize(s));
+        if (R.pool) CK(cudaFree(R.pool));
+        R.pool = nullptr;
+        R.pool_alloc = 0;
+        CK(cudaMalloc((void **)&R.pool, cap * sizeof(uint16_t)));
+        R.pool_alloc = cap;
+        ++R.gen;
+    }
+    return EPSM_OK;
+}
+
 group::Params batch_params(epsm_ctx *c) {
     BatchRes &R = c->batch;
     group::Params p;
@@ -376,8 +423,10 @@ group::Params batch_params(epsm_ctx *c) {
     p.comb = reinterpret_cast<group::SharedTable *>(R.comb);
     p.tables = R.tables;
     p.offsets = R.doff;
-    p.seg_count = c->seg_count;
-    p.seg_mask = c->seg_mask;
+    p.seg_count = R.seg_count;
+    p.seg_off = R.seg_off;
+    p.pool = R.pool;
+    p.pool_ctr = R.pool_ctr;
     p.range_total = R.rt;
     p.err = &c->misc->err;
     p.misc = c->misc;
@@ -470,7 +519,7 @@ void build_batch_graph(epsm_ctx *c) {
     R.graph = g;
     R.up = n_up;
     R.down = n_down;
-    R.graph_seg_cap = c->seg_cap;
+    R.graph_gen = R.gen;
 }
 
 // Window stride K of a pattern in the shared filter of its text's group (0:
@@ -488,31 +537,31 @@ uint32_t shared_stride(uint32_t m) {
 // passes: one group per text (more if its patterns exceed the per-group
 // limits), with a shared filter over its patterns of stride K > 0 and the
 // others run one by one on the staged bytes.
-epsm_status batch_impl(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts,
-                       const uint64_t *ns, const uint8_t *const *patterns, const uint32_t *ms,
-                       uint64_t *positions, uint64_t capacity, uint64_t *offsets,
-                       cudaStream_t s) {
+epsm_status batch_submit(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts,
+                         const uint64_t *ns, const uint8_t *const *patterns, const uint32_t *ms,
+                         uint64_t *positions, uint64_t capacity, cudaStream_t s) {
     using namespace group;
-    // texts shared by several pairs
-    using TextKey = std::pair<uintptr_t, uint64_t>;  // (start, length): same view
-    std::map<TextKey, std::vector<uint32_t>> by_text;
-    std::vector<TextKey> text_order;
-    for (uint32_t j = 0; j < npairs; ++j) {
-        const TextKey key((uintptr_t)texts[j], ns[j]);
-        auto it = by_text.find(key);
-        if (it == by_text.end()) {
-            by_text.emplace(key, std::vector<uint32_t>{j});
-            text_order.push_back(key);
-        } else {
-            it->second.push_back(j);
-        }
-    }
+    // texts shared by several pairs: pairs sorted by (start, length, index),
+    // so each text's pairs are one run in pair order
+    std::vector<uint32_t> order(npairs);
+    for (uint32_t j = 0; j < npairs; ++j) order[j] = j;
+    std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) {
+        if (texts[a] != texts[b]) return (uintptr_t)texts[a] < (uintptr_t)texts[b];
+        if (ns[a] != ns[b]) return ns[a] < ns[b];
+        return a < b;
+    });
+    std::vector<uint32_t> runs;  // run starts in `order`, plus npairs
+    runs.reserve(npairs + 1);
+    for (uint32_t k = 0; k < npairs; ++k)
+        if (k == 0 || texts[order[k]] != texts[order[k - 1]] || ns[order[k]] != ns[order[k - 1]])
+            runs.push_back(k);
+    runs.push_back(npairs);
     std::vector<uint32_t> kstr(npairs, 0u);
     std::vector<uint8_t> multi(npairs, 0);
-    for (const TextKey &key : text_order) {
-        const auto &v = by_text[key];
-        if (v.size() < 2) continue;
-        for (uint32_t j : v) {
+    for (size_t r = 0; r + 1 < runs.size(); ++r) {
+        if (runs[r + 1] - runs[r] < 2) continue;
+        for (uint32_t k = runs[r]; k < runs[r + 1]; ++k) {
+            const uint32_t j = order[k];
             kstr[j] = shared_stride(ms[j]);
             multi[j] = 1;
         }
@@ -523,6 +572,7 @@ epsm_status batch_impl(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts
     std::vector<JobDesc> kept;
     kept.reserve(npairs);
     uint64_t jst = 0;
+    uint64_t starts = 0;  // valid starts over all pairs: a bound on the hits
     uint32_t ntab = 0;
     for (uint32_t i = 0; i < npairs; ++i) {
         const uint32_t m = ms[i];
@@ -543,12 +593,15 @@ epsm_status batch_impl(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts
         jidx[i] = (int32_t)kept.size();
         kept.push_back(D);
         jst += nst;
+        starts += ns[i] - m + 1u;
     }
     const uint32_t nj = (uint32_t)kept.size();
-    if (nj == 0) {
-        for (uint32_t i = 0; i <= npairs; ++i) offsets[i] = 0;
-        return EPSM_OK;
-    }
+    BatchRes &RB = c->batch;
+    RB.pend_jidx = jidx;
+    RB.pend_npairs = npairs;
+    RB.pend_nj = nj;
+    RB.pend_capacity = capacity;
+    if (nj == 0) return mark_done(c, s);
     // groups: per text, shared patterns up to kMaxShared / kMaxEnt entries and
     // individual ones up to kIndivMax per group
     std::vector<GroupDesc> groups;
@@ -556,9 +609,12 @@ epsm_status batch_impl(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts
     gjobs.reserve(nj);
     uint32_t ncomb = 0;
     uint64_t gst = 0;
-    for (const TextKey &key : text_order) {
-        std::vector<uint32_t> sh, ind;
-        for (uint32_t pi : by_text[key]) {
+    std::vector<uint32_t> sh, ind;
+    for (size_t r = 0; r + 1 < runs.size(); ++r) {
+        sh.clear();
+        ind.clear();
+        for (uint32_t k = runs[r]; k < runs[r + 1]; ++k) {
+            const uint32_t pi = order[k];
             if (jidx[pi] < 0) continue;
             (kstr[pi] ? sh : ind).push_back((uint32_t)jidx[pi]);
         }
@@ -593,7 +649,7 @@ epsm_status batch_impl(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts
             G.gstage0 = gst;
             G.nstages = nst;
             G.cfg = k8 | (k4 << 8);
-            G.comb = G.nshared ? ncomb++ : kNone;
+            G.comb = (G.nshared || G.nindiv > 1u) ? ncomb++ : kNone;
             gst += nst;
             groups.push_back(G);
         }
@@ -625,11 +681,16 @@ epsm_status batch_impl(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts
     memcpy(R.hstage + batch_jobs_off(), kept.data(), nj * sizeof(JobDesc));
     memcpy(R.hstage + goff, groups.data(), ng * sizeof(GroupDesc));
     memcpy(R.hstage + gjoff, gjobs.data(), gjobs.size() * sizeof(uint32_t));
-    if ((st = ensure_stream_scratch(c, jst, s)) != EPSM_OK) return st;
+    // hit lists: at most min(capacity, starts) entries, plus the unused tail of
+    // each warp's last pool chunk
+    H.pool_cap = capacity > 0 ? std::min<uint64_t>(capacity, starts) +
+                                    (uint64_t)R.grid * stream::kConsumerWarps * kPoolChunk
+                              : 0;
+    if ((st = ensure_batch_scratch(c, jst * stream::kConsumerWarps, H.pool_cap, s)) != EPSM_OK) return st;
     if ((st = order_after_previous(c, s)) != EPSM_OK) return st;
     const size_t up = gjoff + gjobs.size() * sizeof(uint32_t);
     const size_t down = ((size_t)nj + 1) * sizeof(uint64_t);
-    if (!R.graph_failed && (!R.exec || R.graph_seg_cap != c->seg_cap)) build_batch_graph(c);
+    if (!R.graph_failed && (!R.exec || R.graph_gen != R.gen)) build_batch_graph(c);
     bool launched = false;
     if (!R.graph_failed && R.exec) {
         if (cudaGraphExecMemcpyNodeSetParams1D(R.exec, R.up, R.dstage, R.hstage, up,
@@ -645,16 +706,42 @@ epsm_status batch_impl(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts
     }
     if (!launched) CK(enqueue_batch(c, batch_params(c), up, down, s));
     c->launches += 2;  // table build + batched scan
-    if ((st = mark_done(c, s)) != EPSM_OK) return st;
-    uint32_t err = 0;
-    if ((st = read_misc(c, s, &err)) != EPSM_OK) return st;
+    CK(cudaMemcpyAsync(c->hmisc, c->misc, sizeof(DevMisc), cudaMemcpyDeviceToHost, s));
+    return mark_done(c, s);
+}
+
+// Results of the batch submitted last on c, once its work has completed
+// (the context's event): pair offsets and the status.
+epsm_status batch_complete(epsm_ctx *c, uint64_t *offsets) {
+    BatchRes &R = c->batch;
+    const uint32_t npairs = R.pend_npairs;
+    if (R.pend_nj == 0) {
+        for (uint32_t i = 0; i <= npairs; ++i) offsets[i] = 0;
+        return EPSM_OK;
+    }
+    const uint32_t err = c->hmisc->err;
+    if (err) {
+        CK(cudaMemsetAsync(&c->misc->err, 0, sizeof(uint32_t), c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
     // job offsets -> pair offsets; pairs without stages own an empty range at
     // the next pair's offset
-    offsets[npairs] = R.hoff[nj];
+    const std::vector<int32_t> &jidx = R.pend_jidx;
+    offsets[npairs] = R.hoff[R.pend_nj];
     for (uint32_t i = npairs; i-- > 0;)
         offsets[i] = jidx[i] >= 0 ? R.hoff[jidx[i]] : offsets[i + 1];
     if (err & kErrTimeout) return EPSM_ERR_TIMEOUT;
-    return offsets[npairs] > capacity ? EPSM_ERR_CAPACITY : EPSM_OK;
+    return offsets[npairs] > R.pend_capacity ? EPSM_ERR_CAPACITY : EPSM_OK;
+}
+
+epsm_status batch_impl(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts,
+                       const uint64_t *ns, const uint8_t *const *patterns, const uint32_t *ms,
+                       uint64_t *positions, uint64_t capacity, uint64_t *offsets,
+                       cudaStream_t s) {
+    epsm_status st = batch_submit(c, npairs, texts, ns, patterns, ms, positions, capacity, s);
+    if (st != EPSM_OK) return st;
+    CK(cudaEventSynchronize(c->ev));
+    return batch_complete(c, offsets);
 }
 
 }  // namespace
@@ -944,3 +1031,5 @@ EPSM_API epsm_status epsm_search_static(const uint8_t *text, uint64_t n, const u
     if (launch_stream(D.sms, v, m, p, s) != cudaSuccess) return EPSM_ERR_CUDA;
     return EPSM_OK;
 }
+
+#include "epsm_serve.inc"

@@ -54,8 +54,9 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kEndChain = 0xFFFFu;
 constexpr uint32_t kW8Min = 11;          // patterns this long use 8-byte windows
 constexpr int kRangesPerBlock = 32;      // emit ranges per block (dealt round-robin)
+constexpr uint32_t kPoolChunk = 4096;    // pool entries a warp reserves at a time (>= 2048)
 
-struct JobDesc {
+struct alignas(16) JobDesc {
     SearchJob job;         // text view and pattern
     uint64_t stage0;       // first stage of the pair in the per-pattern numbering
     uint64_t nstages;      // > 0
@@ -67,7 +68,7 @@ struct JobDesc {
     uint32_t ent0;         // shared patterns: index of its first table entry
 };
 
-struct GroupDesc {
+struct alignas(16) GroupDesc {
     SearchJob text;        // text view (pattern unused)
     uint64_t chunk_full0, chunk_full1;
     uint64_t gstage0;      // first stage of the group in the group numbering
@@ -77,8 +78,9 @@ struct GroupDesc {
     uint32_t nindiv;
     uint32_t nent;         // table entries
     uint32_t cfg;          // k8 | k4 << 8: smallest stride of the 8- and 4-byte windows (0: none)
-    uint32_t comb;         // index of its table (kNone if no shared pattern)
+    uint32_t comb;         // index of its table (kNone for a group of one pattern)
 };
+static_assert(sizeof(JobDesc) % 16 == 0 && sizeof(GroupDesc) % 16 == 0, "copied as uint4");
 
 struct Header {
     const GroupDesc *groups;          // ascending gstage0 (in the uploaded staging, after the jobs)
@@ -90,6 +92,7 @@ struct Header {
     uint64_t range_stages;  // pattern stages per emit range
     uint32_t nranges;       // emit ranges (at most kRangesPerBlock x grid)
     uint32_t pad2;
+    uint64_t pool_cap;      // hit-list pool entries
     uint64_t capacity;
     uint64_t *positions;
     uint32_t emit;
@@ -105,7 +108,15 @@ struct SharedTable {
     uint64_t stage0[kMaxShared];     // per-pattern stage numbering
     uint32_t nst[kMaxShared];
     uint32_t m[kMaxShared];
+    // the group's short patterns (direct compare)
+    uint64_t istage0[kIndivMax];
+    int64_t ipmax[kIndivMax];
+    uint32_t iw0[kIndivMax];
+    uint32_t im[kIndivMax];
+    uint32_t inst[kIndivMax];
+    uint32_t ipad[kIndivMax];
 };
+static_assert(sizeof(SharedTable) % 16 == 0, "copied as uint4");
 
 struct Params {
     const Header *hdr;
@@ -113,8 +124,10 @@ struct Params {
     SharedTable *comb;           // one per group with shared patterns
     uint8_t *tables;             // block-variant tables of individual patterns (kTableBytes each)
     uint64_t *offsets;           // per job: exclusive prefix at its first segment; [njobs] = total
-    uint32_t *seg_count;
-    uint16_t *seg_mask;
+    uint32_t *seg_count;         // per pattern segment: hits
+    uint32_t *seg_off;           // per pattern segment with hits: its list in pool
+    uint16_t *pool;              // hit lists: offsets in the segment, ascending
+    uint32_t *pool_ctr;          // entries handed out (zeroed by the table kernel)
     unsigned long long *range_total;  // per emit range (zeroed by the table kernel)
     uint32_t *err;
     DevMisc *misc;
@@ -138,6 +151,8 @@ struct alignas(128) Smem {
     SharedTable tab;                             // table of the current group
     uint64_t stage_id[kRing];
     uint32_t stage_group[kRing];
+    GroupDesc sgroup[kRing];                     // the stage's group, copied by the producer
+    JobDesc sjob[kRing];                         // and its pattern when it has only one
     uint64_t full[kRing];
     uint64_t empty[kRing];
     uint64_t tab_free;                           // mbarrier: every warp is done with the old table
@@ -147,7 +162,10 @@ struct alignas(128) Smem {
     uint16_t hitcnt[kConsumerWarps][kMaxShared];
     uint32_t ovf[kConsumerWarps][kMaxShared / 32];  // patterns whose hits did not fit
     VCtx vc[kConsumerWarps];
-    uint16_t emit_stage[kConsumerWarps][32 * 16];
+    uint32_t mbuf[kConsumerWarps][kSegChunks];   // chunk masks of one shared pattern
+    uint16_t stage16[kConsumerWarps][32 * 16];   // one step's hit offsets, before the pool store
+    uint32_t pcur[kConsumerWarps];               // warp's pool chunk: next entry
+    uint32_t pend[kConsumerWarps];               //   and its end
     uint32_t scan_tmp[kConsumerWarps];
     uint64_t scan_tmp64[kConsumerWarps];
     uint64_t range_excl[kRangesPerBlock];  // output offset of each range the block emits
@@ -175,6 +193,7 @@ __global__ void build_group_tables_kernel(const Params P) {
     const Header H = *P.hdr;
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < H.nranges; r += gridDim.x * blockDim.x)
         P.range_total[r] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *P.pool_ctr = 0u;
     // block-variant tables, one block per job
     for (uint32_t j = blockIdx.x; j < H.njobs; j += gridDim.x) {
         const JobDesc &D = P.jobs[j];
@@ -199,7 +218,7 @@ __global__ void build_group_tables_kernel(const Params P) {
     for (uint32_t g = blockIdx.x; g < H.ngroups; g += gridDim.x) {
         const GroupDesc &G = H.groups[g];
         if (G.comb == kNone) continue;
-        SharedTable &T = P.comb[G.comb];
+        SharedTable &T = P.comb[G.comb];  // (groups of more than one pattern)
         for (int i = threadIdx.x; i < kSlots; i += blockDim.x) T.head[i] = 0u;
         for (uint32_t i = threadIdx.x; i < G.nshared; i += blockDim.x) {
             const JobDesc &D = P.jobs[H.group_jobs[G.job0 + i]];
@@ -208,6 +227,14 @@ __global__ void build_group_tables_kernel(const Params P) {
             T.stage0[i] = D.stage0;
             T.nst[i] = (uint32_t)D.nstages;
             T.m[i] = D.job.pat.m;
+        }
+        for (uint32_t i = threadIdx.x; i < G.nindiv; i += blockDim.x) {
+            const JobDesc &D = P.jobs[H.group_jobs[G.job0 + G.nshared + i]];
+            T.istage0[i] = D.stage0;
+            T.ipmax[i] = D.job.pmax;
+            T.iw0[i] = D.job.pat.w[0];
+            T.im[i] = D.job.pat.m;
+            T.inst[i] = (uint32_t)D.nstages;
         }
         __syncthreads();
         // entries: (pattern i, j) for j < K_i; insertion pushes on the slot's chain
@@ -274,10 +301,27 @@ __device__ __forceinline__ void producer(const Params &P, const Header &H, Smem 
             const int s = issued % kRing;
             const uint32_t n = issued / kRing;
             if (n > 0 && !mbar_wait(&S.empty[s], (n - 1) & 1)) { failed = true; break; }
+            const uint32_t prev = hint;
             hint = find_group(H.groups, H.ngroups, st, hint);
             const GroupDesc &G = H.groups[hint];
             S.stage_id[s] = st;
             S.stage_group[s] = hint;
+            // the consumers read the stage's descriptors from shared memory
+            // (copied again only when the group changes)
+            const int sp = (s + kRing - 1) % kRing;
+            if (issued == 0 || hint != prev || S.stage_group[sp] != hint) {
+                const uint4 *gs = reinterpret_cast<const uint4 *>(&G);
+                uint4 *gd = reinterpret_cast<uint4 *>(&S.sgroup[s]);
+                for (int k = 0; k < (int)(sizeof(GroupDesc) / 16); ++k) gd[k] = gs[k];
+                if (G.nshared == 0u && G.nindiv == 1u) {
+                    const uint4 *js = reinterpret_cast<const uint4 *>(&P.jobs[H.group_jobs[G.job0]]);
+                    uint4 *jd = reinterpret_cast<uint4 *>(&S.sjob[s]);
+                    for (int k = 0; k < (int)(sizeof(JobDesc) / 16); ++k) jd[k] = js[k];
+                }
+            } else {
+                S.sgroup[s] = S.sgroup[sp];
+                S.sjob[s] = S.sjob[sp];
+            }
             const uint64_t c0 = (st - G.gstage0) * kStageChunks;
             const uint64_t a = c0 > G.chunk_full0 ? c0 : G.chunk_full0;
             uint64_t b = c0 + kStageChunks + 1u;
@@ -299,9 +343,98 @@ __device__ __forceinline__ void producer(const Params &P, const Header &H, Smem 
     for (uint32_t i = lo; i < issued; ++i) mbar_wait(&S.full[i % kRing], (i / kRing) & 1);
 }
 
+// Phase-1 result of one pattern segment (a whole warp; lane l holds the hit
+// masks of chunks 32u + l): the count, added to its emit range's total, and,
+// when positions are wanted, the sorted list of hit offsets in the segment
+// (chunk * 16 + bit) in the warp's current pool chunk.
+__device__ __noinline__ void store_list_emit(const Params &P, const Header &H, Smem &S, uint64_t st,
+                                             uint64_t seg, uint32_t h0, uint32_t h1, uint32_t h2,
+                                             uint32_t h3, int w, int lane) {
+    const uint32_t h[4] = {h0, h1, h2, h3};
+    uint32_t c[4], inc[4], T[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        c[u] = __popc(h[u]);
+        inc[u] = c[u];
+    }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t t = __shfl_up_sync(kFull, inc[u], d);
+            if (lane >= d) inc[u] += t;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) T[u] = __shfl_sync(kFull, inc[u], 31);
+    const uint32_t total = T[0] + T[1] + T[2] + T[3];
+    uint32_t base = 0u;
+    if (lane == 0) {
+        P.seg_count[seg] = total;
+        atomicAdd(&P.range_total[st / H.range_stages], (unsigned long long)total);
+        if (S.pcur[w] + total > S.pend[w]) {
+            const uint32_t b = atomicAdd(P.pool_ctr, kPoolChunk);
+            S.pcur[w] = b;
+            S.pend[w] = (uint64_t)b + kPoolChunk <= H.pool_cap ? b + kPoolChunk : b;
+        }
+        if (S.pcur[w] + total <= S.pend[w]) {
+            base = S.pcur[w];
+            S.pcur[w] += total;
+        } else {
+            base = kNone;  // pool exhausted: no positions for this segment
+            atomicOr(P.err, kErrCapacity);
+        }
+        P.seg_off[seg] = base;
+    }
+    base = __shfl_sync(kFull, base, 0);
+    if (base == kNone) return;
+    // each step's offsets are put in order in shared memory, then stored to
+    // the pool with consecutive lanes on consecutive entries
+    uint16_t *stg = S.stage16[w];
+    uint32_t before = 0u;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        if (T[u] == 0u) continue;
+        uint32_t k = inc[u] - c[u];
+        uint32_t hh = h[u];
+        while (hh) {
+            const uint32_t b = (uint32_t)(__ffs(hh) - 1);
+            hh &= hh - 1u;
+            stg[k++] = (uint16_t)((32u * u + (uint32_t)lane) * 16u + b);
+        }
+        __syncwarp();
+        for (uint32_t q = (uint32_t)lane; q < T[u]; q += 32u) P.pool[base + before + q] = stg[q];
+        __syncwarp();
+        before += T[u];
+    }
+}
+
+// Phase-1 result of one pattern segment (a whole warp; lane l holds the hit
+// masks of chunks 32u + l): the count, added to its emit range's total, and,
+// when positions are wanted, the sorted list of hit offsets in the segment
+// (chunk * 16 + bit) in the warp's current pool chunk (out of line).
+__device__ __forceinline__ void store_list(const Params &P, const Header &H, Smem &S, uint64_t st,
+                                           uint64_t seg, uint32_t h0, uint32_t h1, uint32_t h2,
+                                           uint32_t h3, int w, int lane) {
+    const uint32_t any = __any_sync(kFull, (h0 | h1 | h2 | h3) != 0u);
+    if (!any) {
+        if (lane == 0) P.seg_count[seg] = 0u;
+        return;
+    }
+    if (H.emit) {
+        store_list_emit(P, H, S, st, seg, h0, h1, h2, h3, w, lane);
+        return;
+    }
+    const uint32_t total = warp_sum(__popc(h0) + __popc(h1) + __popc(h2) + __popc(h3));
+    if (lane == 0) {
+        P.seg_count[seg] = total;
+        atomicAdd(&P.range_total[st / H.range_stages], (unsigned long long)total);
+    }
+}
+
 // Single-search variant of one individual pattern on the staged stage, stored
 // as its segment.
-__device__ __noinline__ void plain_job(const Params &P, const Header &H, const JobDesc &D,
+__device__ __noinline__ void plain_job(const Params &P, const Header &H, Smem &S, const JobDesc &D,
                                        const uint8_t *buf, uint64_t ls, int w, int lane) {
     const uint64_t c0 = ls * kStageChunks;
     const BcastWords Bw(D.job.pat);
@@ -309,16 +442,14 @@ __device__ __noinline__ void plain_job(const Params &P, const Header &H, const J
     const uint32_t *pb = tb ? reinterpret_cast<const uint32_t *>(tb + kHashSlots) : nullptr;
     const uint64_t cf0 = (D.job.delta + 15u) / 16u, cf1 = D.job.lim / 16u;
     uint32_t h[4] = {0u, 0u, 0u, 0u};
-    uint32_t cnt;
-    switch (D.variant) {
-        case V_DIRECT: cnt = stage_hits<V_DIRECT, 0>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
-        case V_PREFIX4: cnt = stage_hits<V_PREFIX4, 4>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
-        case V_PREFIX8: cnt = stage_hits<V_PREFIX8, 8>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
-        default: cnt = stage_hits<V_BLOCK8, 8>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
+    switch (D.variant) {  // (store_list counts the hits from the masks)
+        case V_DIRECT: stage_hits<V_DIRECT, 0>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
+        case V_PREFIX4: stage_hits<V_PREFIX4, 4>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
+        case V_PREFIX8: stage_hits<V_PREFIX8, 8>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
+        default: stage_hits<V_BLOCK8, 8>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
     }
     const uint64_t st = D.stage0 + ls;
-    store_segment(P.seg_count, P.seg_mask, P.range_total, H.range_stages, st,
-                  st * kConsumerWarps + (uint64_t)w, cnt, h, H.emit != 0, lane);
+    store_list(P, H, S, st, st * kConsumerWarps + (uint64_t)w, h[0], h[1], h[2], h[3], w, lane);
 }
 
 // t[P..P+m) == p (pattern words pw), read from the staged bytes when the stage
@@ -466,7 +597,6 @@ __device__ __noinline__ void pattern_pass(const Params &P, const Header &H, cons
     const int64_t pmax = V.lim - (int64_t)m;
     const int src = (lane + 1) & 31;
     uint32_t h[4];
-    uint32_t cnt = 0u;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const uint4 cur = ch[u];
@@ -490,11 +620,9 @@ __device__ __noinline__ void pattern_pass(const Params &P, const Header &H, cons
             if (verify_at(pw, m, p0 + bit, V)) hh |= 1u << bit;
         }
         h[u] = hh;
-        cnt += __popc(hh);
     }
     const uint64_t st = S.tab.stage0[i] + ls;
-    store_segment(P.seg_count, P.seg_mask, P.range_total, H.range_stages, st,
-                  st * kConsumerWarps + (uint64_t)w, cnt, h, H.emit != 0, lane);
+    store_list(P, H, S, st, st * kConsumerWarps + (uint64_t)w, h[0], h[1], h[2], h[3], w, lane);
 }
 
 // Writes the segment of every shared pattern: count 0 for patterns without
@@ -504,7 +632,7 @@ __device__ __forceinline__ void finish_shared(const Params &P, const Header &H, 
                                               Smem &S, uint64_t ls, int w, int lane) {
     const uint32_t nS = G.nshared;
     const uint32_t nh = S.nhits[w] < (uint32_t)kHitCap ? S.nhits[w] : (uint32_t)kHitCap;
-    uint32_t *mbuf = reinterpret_cast<uint32_t *>(S.emit_stage[w]);  // 128 chunk masks
+    uint32_t *mbuf = S.mbuf[w];
     for (uint32_t i0 = 0; i0 < nS; i0 += 32) {
         const uint32_t i = i0 + (uint32_t)lane;
         const bool valid = i < nS && ls < S.tab.nst[i < nS ? i : 0];
@@ -525,16 +653,13 @@ __device__ __forceinline__ void finish_shared(const Params &P, const Header &H, 
             }
             __syncwarp();
             uint32_t h[4];
-            uint32_t cnt = 0u;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 h[u] = mbuf[u * 32 + lane];
-                cnt += __popc(h[u]);
             }
             __syncwarp();
             const uint64_t st = S.tab.stage0[ii] + ls;
-            store_segment(P.seg_count, P.seg_mask, P.range_total, H.range_stages, st,
-                          st * kConsumerWarps + (uint64_t)w, cnt, h, H.emit != 0, lane);
+            store_list(P, H, S, st, st * kConsumerWarps + (uint64_t)w, h[0], h[1], h[2], h[3], w, lane);
         }
         uint32_t dense = __ballot_sync(kFull, over);
         while (dense) {
@@ -602,7 +727,7 @@ __device__ __forceinline__ void shared_filter_any(const Params &P, const Header 
 // The group's short patterns (m <= 4) on one staged stage: the packed window
 // compare of Section 3.2 for each of them on the segment loaded once.
 __device__ __noinline__ void direct_jobs(const Params &P, const Header &H, const GroupDesc &G,
-                                         const uint8_t *buf, uint64_t ls, int w, int lane) {
+                                         Smem &S, const uint8_t *buf, uint64_t ls, int w, int lane) {
     const uint64_t c0 = ls * kStageChunks;
     uint4 ch[4];
     uint4 halo;
@@ -617,17 +742,15 @@ __device__ __noinline__ void direct_jobs(const Params &P, const Header &H, const
     const int64_t sp0 = (int64_t)((c0 + (uint64_t)w * kSegChunks) * 16u);
     const int64_t delta = (int64_t)G.text.delta;
     for (uint32_t i = 0; i < G.nindiv; ++i) {
-        const JobDesc &D = P.jobs[H.group_jobs[G.job0 + G.nshared + i]];
-        if (ls >= D.nstages) continue;
-        const uint32_t m = D.job.pat.m, p0w = D.job.pat.w[0];
+        if (ls >= S.tab.inst[i]) continue;
+        const uint32_t m = S.tab.im[i], p0w = S.tab.iw0[i];
         const uint32_t b0 = bcast_byte(p0w, 0), b1 = bcast_byte(p0w, 1);
         const uint32_t b2 = bcast_byte(p0w, 2), b3 = bcast_byte(p0w, 3);
         const uint32_t mk1 = m <= 1u ? 0u : 0xFFFFFFFFu, mk2 = m <= 2u ? 0u : 0xFFFFFFFFu;
         const uint32_t mk3 = m <= 3u ? 0u : 0xFFFFFFFFu;
-        const int64_t pmax = D.job.pmax;
+        const int64_t pmax = S.tab.ipmax[i];
         const bool interior = sp0 >= delta && sp0 + (int64_t)(kSegChunks * 16) - 1 <= pmax;
         uint32_t h[4];
-        uint32_t cnt = 0u;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const uint32_t R[5] = {ch[u].x, ch[u].y, ch[u].z, ch[u].w, nx[u]};
@@ -644,11 +767,9 @@ __device__ __noinline__ void direct_jobs(const Params &P, const Header &H, const
                 hh &= range_mask(delta - p0, pmax - p0);
             }
             h[u] = hh;
-            cnt += __popc(hh);
         }
-        const uint64_t st = D.stage0 + ls;
-        store_segment(P.seg_count, P.seg_mask, P.range_total, H.range_stages, st,
-                      st * kConsumerWarps + (uint64_t)w, cnt, h, H.emit != 0, lane);
+        const uint64_t st = S.tab.istage0[i] + ls;
+        store_list(P, H, S, st, st * kConsumerWarps + (uint64_t)w, h[0], h[1], h[2], h[3], w, lane);
     }
 }
 
@@ -664,7 +785,7 @@ __device__ __forceinline__ void consumer(const Params &P, const Header &H, Smem 
         const uint64_t st = S.stage_id[s];
         if (st == kEndStage) break;
         const uint32_t g = S.stage_group[s];
-        const GroupDesc &G = H.groups[g];
+        const GroupDesc &G = S.sgroup[s];
         const uint64_t ls = st - G.gstage0;
         const uint8_t *buf = S.buf[s];
         // load the group's table: every consumer warp reaches this stage;
@@ -685,10 +806,10 @@ __device__ __forceinline__ void consumer(const Params &P, const Header &H, Smem 
         // individual patterns: a pattern alone on its text runs its own
         // variant; the short patterns of a shared text run together
         if (G.nindiv == 1u && G.nshared == 0u) {
-            const JobDesc &D = P.jobs[H.group_jobs[G.job0]];
-            if (ls < D.nstages) plain_job(P, H, D, buf, ls, w, lane);
+            const JobDesc &D = S.sjob[s];
+            if (ls < D.nstages) plain_job(P, H, S, D, buf, ls, w, lane);
         } else if (G.nindiv) {
-            direct_jobs(P, H, G, buf, ls, w, lane);
+            direct_jobs(P, H, G, S, buf, ls, w, lane);
         }
         if (G.nshared) shared_filter_any(P, H, G, S, buf, ls, w, lane);
         __syncwarp();
@@ -710,11 +831,16 @@ __device__ __forceinline__ uint32_t first_job_from(const JobDesc *jobs, uint32_t
     return lo;
 }
 
+// Emission of the pattern stages [st0, st1) with output offset base0:
+// batches of 256 segments, a block scan of their counts, then each warp
+// copies the hit lists of its 32 segments as one flat sequence (lane q takes
+// hits q, q + 32, ...; the segment of a hit is found by a binary search over
+// the warp's inclusive counts), so the stores of a warp are consecutive.
 __device__ __forceinline__ void emit_range(const Params &P, const Header &H, Smem &S, uint64_t st0,
-                                           uint64_t st1, uint64_t cta_excl, int w, int lane) {
+                                           uint64_t st1, uint64_t base0, int w, int lane) {
     const int t = w * 32 + lane;
     const uint64_t seg0 = st0 * kConsumerWarps, seg1 = st1 * kConsumerWarps;
-    uint64_t base = cta_excl;
+    uint64_t base = base0;
     uint32_t jcur = first_job_from(P.jobs, H.njobs, st0);
     uint32_t wj = jcur > 0 ? jcur - 1u : 0u;
     for (uint64_t sb = seg0; sb < seg1; sb += kConsumerWarps * 32) {
@@ -740,19 +866,39 @@ __device__ __forceinline__ void emit_range(const Params &P, const Header &H, Sme
                 ++jcur;
             }
         }
-        const uint32_t todo = __ballot_sync(kFull, c != 0u);
-        if (todo && H.emit) {
-            emit_list(todo, sb + (uint64_t)w * 32u, excl, P.seg_mask, lane,
-                      [&](uint64_t sj, uint64_t ej, uint2 packed) {
-                          const uint64_t stg = sj / kConsumerWarps;
-                          while (wj + 1u < H.njobs && P.jobs[wj + 1u].stage0 <= stg) ++wj;
-                          const JobDesc &D = P.jobs[wj];
-                          const int64_t s0 = (int64_t)(((stg - D.stage0) * kStageChunks +
-                                                        (sj % kConsumerWarps) * kSegChunks) * 16u) +
-                                             D.off - (int64_t)D.job.delta;
-                          emit_segment(H.positions, H.capacity, P.err, s0, ej, packed,
-                                       S.emit_stage[w], lane);
-                      });
+        const uint32_t wtotal = __shfl_sync(kFull, inc, 31);
+        if (wtotal != 0u && H.emit) {
+            // this lane's segment: pool list and start of its first chunk
+            uint32_t off = 0u;
+            int64_t s0 = 0;
+            if (c != 0u) {
+                off = P.seg_off[seg];
+                const uint64_t stg = seg / kConsumerWarps;
+                while (wj + 1u < H.njobs && P.jobs[wj + 1u].stage0 <= stg) ++wj;
+                const JobDesc &D = P.jobs[wj];
+                s0 = (int64_t)(((stg - D.stage0) * kStageChunks + (seg % kConsumerWarps) * kSegChunks) * 16u) +
+                     D.off - (int64_t)D.job.delta;
+            }
+            const uint64_t wexcl = __shfl_sync(kFull, excl, 0);
+            if (lane == 0 && wexcl + wtotal > H.capacity) atomicOr(P.err, kErrCapacity);
+            for (uint32_t q0 = 0; q0 < wtotal; q0 += 32u) {
+                const uint32_t q = q0 + (uint32_t)lane;
+                // segment j: the first lane whose inclusive count exceeds q
+                uint32_t j = 0u;
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) {
+                    const uint32_t v = __shfl_sync(kFull, inc, (int)(j + (uint32_t)d - 1u));
+                    if (v <= q) j += (uint32_t)d;
+                }
+                j = j < 31u ? j : 31u;
+                const uint32_t ij = __shfl_sync(kFull, inc, (int)j);
+                const uint32_t cj = __shfl_sync(kFull, c, (int)j);
+                const uint32_t oj = __shfl_sync(kFull, off, (int)j);
+                const int64_t sj = __shfl_sync(kFull, s0, (int)j);
+                const uint64_t idx = wexcl + q;
+                if (q < wtotal && oj != kNone && idx < H.capacity)
+                    H.positions[idx] = (uint64_t)(sj + (int64_t)P.pool[oj + (q - (ij - cj))]);
+            }
         }
         base += btotal;
         consumer_sync();
@@ -776,6 +922,7 @@ __global__ void __launch_bounds__(stream::kThreadsStream, stream::kMaxBlocksPerS
         }
         mbar_init(&S.tab_free, kConsumerWarps);
         mbar_init(&S.tab_ready, kConsumerWarps);
+        for (int k = 0; k < kConsumerWarps; ++k) S.pcur[k] = S.pend[k] = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();

@@ -1,6 +1,6 @@
 """C-ABI checks that need no GPU: the library builds, loads, and exports every
-entry point include/epsm.h declares; host-only paths validate arguments; the
-product package never touches the oracle."""
+entry point the headers under include/ declare; host-only paths validate
+arguments; the product package never touches the oracle."""
 import ctypes
 import os
 import re
@@ -10,7 +10,8 @@ import sys
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "epsm.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
 def _built_lib():
@@ -20,15 +21,18 @@ def _built_lib():
 
 
 def declared_functions():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(epsm_[a-z_0-9]+)\s*\(", src)))
+    names = set()
+    for h in HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(epsm_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("epsm_create", "epsm_search", "epsm_search_batch", "epsm_destroy",
-                     "epsm_status_str"):
+                     "epsm_status_str", "epsm_server_create", "epsm_server_submit",
+                     "epsm_server_poll", "epsm_server_replay"):
         assert required in names
 
 
@@ -58,6 +62,20 @@ def test_status_strings_and_null_context():
     assert lib.epsm_variant_for(None, 4) == 0
 
 
+def test_server_arguments_checked_on_the_host():
+    _built_lib()
+    import paper_1209_6449_gb300 as epsm
+    lib = epsm._lib
+    rid = ctypes.c_uint64()
+    assert lib.epsm_server_create(None, 0, None) == 1
+    assert lib.epsm_server_destroy(None) == 0
+    assert lib.epsm_server_submit(None, 0, b"ab", 2, ctypes.byref(rid)) == 1
+    assert lib.epsm_server_upload(None, b"ab", 2, ctypes.byref(rid)) == 1
+    assert lib.epsm_server_poll(None, None, 4, 0) == 0
+    assert lib.epsm_server_release(None, 1) == 1
+    assert lib.epsm_server_read(None, 1, None, 0) == 1
+
+
 def test_missing_library_fails_loudly(tmp_path):
     _built_lib()
     from paper_1209_6449_gb300 import _native
@@ -69,7 +87,7 @@ def test_package_does_not_reach_the_oracle():
     pkg = os.path.join(ROOT, "paper_1209_6449_gb300")
     for dirpath, _, files in os.walk(pkg):
         for f in files:
-            if f.endswith((".py", ".cu", ".cuh", ".h")):
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".inc")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "liboracle" not in txt and "epsm_oracle" not in txt, f
