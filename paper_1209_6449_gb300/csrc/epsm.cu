@@ -102,7 +102,8 @@ struct BatchRes {
     uint64_t gen = 1;                // bumped when a buffer the graph uses moves
     uint64_t graph_gen = 0;          // generation the graph was built with
     bool graph_failed = false;       // a build failed once: launch directly
-    int grid = 0;
+    int grid = 0;   // filter kernel blocks
+    int egrid = 0;  // emission kernel blocks
 };
 
 constexpr size_t kBatchHdrBytes = 128;  // Header, padded to keep JobDesc aligned
@@ -335,6 +336,19 @@ int batch_grid(int sms) {
     return (int)std::min<uint64_t>((uint64_t)sms * per_sm, stream::kMaxBlocks);
 }
 
+// Blocks of the emission kernel: as many as fit (it is latency bound).
+int emit_grid(int sms) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, group_emit_kernel, group::kEmitThreads, 0) !=
+            cudaSuccess)
+            return 0;
+        per_sm = std::max(1, b);
+    }
+    return sms * per_sm;
+}
+
 void drop_graph(BatchRes &R) {
     if (R.exec) cudaGraphExecDestroy(R.exec);
     if (R.graph) cudaGraphDestroy(R.graph);
@@ -375,7 +389,7 @@ epsm_status ensure_batch(epsm_ctx *c, uint32_t njobs, uint32_t ncomb, cudaStream
         if (R.comb) CK(cudaFree(R.comb));
         R.comb = nullptr;
         R.comb_cap = 0;
-        CK(cudaMalloc((void **)&R.comb, (size_t)cc * sizeof(group::SharedTable)));
+        CK(cudaMalloc((void **)&R.comb, (size_t)cc * sizeof(group::GroupTables)));
         R.comb_cap = cc;
     }
     return EPSM_OK;
@@ -420,7 +434,7 @@ group::Params batch_params(epsm_ctx *c) {
     memset(&p, 0, sizeof(p));
     p.hdr = reinterpret_cast<const group::Header *>(R.dstage);
     p.jobs = reinterpret_cast<const group::JobDesc *>(R.dstage + batch_jobs_off());
-    p.comb = reinterpret_cast<group::SharedTable *>(R.comb);
+    p.comb = reinterpret_cast<group::GroupTables *>(R.comb);
     p.tables = R.tables;
     p.offsets = R.doff;
     p.seg_count = R.seg_count;
@@ -443,15 +457,16 @@ cudaError_t enqueue_batch(epsm_ctx *c, const group::Params &p, size_t up, size_t
     if (e != cudaSuccess) return e;
     group::build_group_tables_kernel<<<kTableGrid, 256, 0, s>>>(p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    void *args[] = {(void *)&p};
-    e = cudaLaunchCooperativeKernel((const void *)group_kernel, dim3(R.grid),
-                                    dim3(stream::kThreadsStream), args, sizeof(group::Smem), s);
-    if (e != cudaSuccess) return e;
+    group_kernel<<<R.grid, stream::kThreadsStream, sizeof(group::Smem), s>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    group_emit_kernel<<<R.egrid, group::kEmitThreads, 0, s>>>(p);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return cudaMemcpyAsync(R.hoff, R.doff, down, cudaMemcpyDeviceToHost, s);
 }
 
 // Builds the submission as an explicit graph sized for the full capacity
-// (upload -> table build -> cooperative batched scan -> offsets download);
+// (upload -> table build -> filter kernel -> emission kernel -> offsets
+// download);
 // the two copies' sizes are set per launch.  Any failure leaves direct
 // launches in use (the reason is kept in the context's error string).
 void build_batch_graph(epsm_ctx *c) {
@@ -480,8 +495,9 @@ void build_batch_graph(epsm_ctx *c) {
         kp.kernelParams = args;
         e = cudaGraphAddKernelNode(&n_tab, g, &n_up, 1, &kp);
     }
+    cudaGraphNode_t n_emit = nullptr;
     if (e == cudaSuccess) {
-        what = "kernel node (scan)";
+        what = "kernel node (filter)";
         cudaKernelNodeParams kp;
         memset(&kp, 0, sizeof(kp));
         void *args[] = {(void *)&p};
@@ -491,17 +507,21 @@ void build_batch_graph(epsm_ctx *c) {
         kp.sharedMemBytes = sizeof(group::Smem);
         kp.kernelParams = args;
         e = cudaGraphAddKernelNode(&n_scan, g, &n_tab, 1, &kp);
-        if (e == cudaSuccess) {
-            what = "cooperative attribute";
-            cudaLaunchAttributeValue v;
-            memset(&v, 0, sizeof(v));
-            v.cooperative = 1;
-            e = cudaGraphKernelNodeSetAttribute(n_scan, cudaLaunchAttributeCooperative, &v);
-        }
+    }
+    if (e == cudaSuccess) {
+        what = "kernel node (emission)";
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof(kp));
+        void *args[] = {(void *)&p};
+        kp.func = (void *)group_emit_kernel;
+        kp.gridDim = dim3(R.egrid);
+        kp.blockDim = dim3(group::kEmitThreads);
+        kp.kernelParams = args;
+        e = cudaGraphAddKernelNode(&n_emit, g, &n_scan, 1, &kp);
     }
     if (e == cudaSuccess) {
         what = "memcpy node (download)";
-        e = cudaGraphAddMemcpyNode1D(&n_down, g, &n_scan, 1, R.hoff, R.doff, down,
+        e = cudaGraphAddMemcpyNode1D(&n_down, g, &n_emit, 1, R.hoff, R.doff, down,
                                      cudaMemcpyDeviceToHost);
     }
     if (e == cudaSuccess) {
@@ -659,16 +679,20 @@ epsm_status batch_submit(epsm_ctx *c, uint32_t npairs, const uint8_t *const *tex
     if ((st = ensure_batch(c, std::max(nj, ng), ncomb, s)) != EPSM_OK) return st;
     BatchRes &R = c->batch;
     if (R.grid == 0) R.grid = batch_grid(c->sms);
-    if (R.grid == 0) return EPSM_ERR_CUDA;
+    if (R.egrid == 0) R.egrid = emit_grid(c->sms);
+    if (R.grid == 0 || R.egrid == 0) return EPSM_ERR_CUDA;
     Header &H = *reinterpret_cast<Header *>(R.hstage);
     memset(&H, 0, sizeof(H));
     H.ngroups = ng;
     H.njobs = nj;
     H.gstages = gst;
     H.jstages = jst;
-    // emit ranges: up to kRangesPerBlock per block, dealt round-robin so that
-    // dense and sparse patterns' stages spread over all blocks
-    const uint64_t nr_want = std::min<uint64_t>(jst, (uint64_t)kRangesPerBlock * (uint64_t)R.grid);
+    // emit ranges, claimed dynamically by the emission kernel's blocks: many
+    // (dense ranges take longer than sparse ones), each at least one batch of
+    // 256 stages (one per emission thread), at most the range-total buffer
+    const uint64_t per_batch = (uint64_t)group::kEmitThreads;
+    const uint64_t nr_want = std::max<uint64_t>(
+        1, std::min<uint64_t>(jst / per_batch, (uint64_t)kRangesPerBlock * stream::kMaxBlocks));
     H.range_stages = (jst + nr_want - 1) / nr_want;
     H.nranges = (uint32_t)((jst + H.range_stages - 1) / H.range_stages);
     H.capacity = capacity;

@@ -30,10 +30,13 @@
 // filter (dense hits).  Patterns with m <= 4 and patterns alone on their text
 // run their own single-search variant on the staged bytes.
 //
-// Phases: claim group stages dynamically and stream them through a ring of
-// stage buffers; grid barrier; per-block prefix over range totals; ordered emit
-// of the block's range of pattern stages (see epsm_stream.cuh).  Every wait is
-// bounded in time.
+// Two kernels.  group_kernel (persistent, two blocks per SM): claim group
+// stages dynamically and stream them through a ring of stage buffers; for
+// every pattern segment write its hit count (added to its emit range's total)
+// and its hits (offset list or chunk masks) into a pool.  group_emit_kernel
+// (as many blocks as fit): each block takes the prefix of the range totals,
+// then claims emit ranges dynamically and writes their positions in order.
+// Every wait is bounded in time.
 #pragma once
 
 #include "epsm_stream.cuh"
@@ -46,15 +49,17 @@ using namespace stream;
 constexpr int kRing = 3;                 // stages in flight per block
 constexpr int kSlotBits = 12;
 constexpr int kSlots = 1 << kSlotBits;   // head slots of the shared table
-constexpr int kMaxEnt = 512;             // window entries per group
-constexpr int kMaxShared = 128;          // shared-filter patterns per group
+constexpr int kMaxEnt = 1536;            // window entries per group
+constexpr int kMaxShared = 256;          // shared-filter patterns per group
 constexpr int kIndivMax = 64;            // single-variant patterns per group
 constexpr int kHitCap = 256;             // confirmed hits per warp and stage
 constexpr uint32_t kNone = 0xFFFFFFFFu;
-constexpr uint32_t kEndChain = 0xFFFFu;
+constexpr uint32_t kEndChain = 0x7FFu;  // (entry indices have 11 bits)
 constexpr uint32_t kW8Min = 11;          // patterns this long use 8-byte windows
 constexpr int kRangesPerBlock = 32;      // emit ranges per block (dealt round-robin)
 constexpr uint32_t kPoolChunk = 4096;    // pool entries a warp reserves at a time (>= 2048)
+constexpr uint32_t kMaskMin = 128;       // segments with this many hits store chunk masks
+constexpr uint32_t kMaskFlag = 0x80000000u;  // seg_off: the segment's pool entry holds masks
 
 struct alignas(16) JobDesc {
     SearchJob job;         // text view and pattern
@@ -100,11 +105,13 @@ struct Header {
 };
 
 // The shared table of one group (built in global memory, copied to shared
-// memory when a block starts on the group).
+// memory when a block starts on the group).  An entry is {window's first 4
+// bytes, meta}: meta = next | j << 11 | log2 K << 14 | w4 << 16 | i << 17.  An
+// 8-byte window is compared on its first 4 bytes after its 16-bit tag matched;
+// the full check decides.
 struct SharedTable {
     uint32_t head[kSlots];           // 0, or tag << 16 | (entry + 1); tag 0: several entries
-    uint4 ent[kMaxEnt];              // {lo, hi, meta, next}; meta = i << 8 | w4 << 7 | log2 K << 4 | j
-    uint32_t pw[kMaxShared][8];      // pattern words
+    uint2 ent[kMaxEnt];
     uint64_t stage0[kMaxShared];     // per-pattern stage numbering
     uint32_t nst[kMaxShared];
     uint32_t m[kMaxShared];
@@ -118,10 +125,17 @@ struct SharedTable {
 };
 static_assert(sizeof(SharedTable) % 16 == 0, "copied as uint4");
 
+// A group's table and its patterns' words (read from global memory only by
+// the full check of a candidate).
+struct GroupTables {
+    SharedTable t;
+    uint32_t pw[kMaxShared][8];
+};
+
 struct Params {
     const Header *hdr;
     const JobDesc *jobs;
-    SharedTable *comb;           // one per group with shared patterns
+    GroupTables *comb;           // one per group of more than one pattern
     uint8_t *tables;             // block-variant tables of individual patterns (kTableBytes each)
     uint64_t *offsets;           // per job: exclusive prefix at its first segment; [njobs] = total
     uint32_t *seg_count;         // per pattern segment: hits
@@ -142,6 +156,7 @@ struct VCtx {
     int64_t delta;         // first internal byte of the text
     int64_t lim;           // first internal byte past the text
     int64_t sbase;         // internal byte of buf[0]
+    const uint32_t *gpw;   // the group's pattern words (global)
     uint32_t inside;       // the whole stage buffer holds text bytes
     uint32_t pad;
 };
@@ -162,15 +177,26 @@ struct alignas(128) Smem {
     uint16_t hitcnt[kConsumerWarps][kMaxShared];
     uint32_t ovf[kConsumerWarps][kMaxShared / 32];  // patterns whose hits did not fit
     VCtx vc[kConsumerWarps];
-    uint32_t mbuf[kConsumerWarps][kSegChunks];   // chunk masks of one shared pattern
-    uint16_t stage16[kConsumerWarps][32 * 16];   // one step's hit offsets, before the pool store
+    alignas(16) uint16_t stage16[kConsumerWarps][32 * 16];  // one step's hit offsets, before the pool store;
+                                                 // also a shared pattern's 128 chunk masks
     uint32_t pcur[kConsumerWarps];               // warp's pool chunk: next entry
     uint32_t pend[kConsumerWarps];               //   and its end
-    uint32_t scan_tmp[kConsumerWarps];
-    uint64_t scan_tmp64[kConsumerWarps];
-    uint64_t range_excl[kRangesPerBlock];  // output offset of each range the block emits
-    uint64_t total;
-    uint64_t batch_excl[kConsumerWarps * 32];
+};
+
+// Shared memory of the emission kernel (one block: 8 warps).
+constexpr int kEmitWarps = 8;
+constexpr int kEmitThreads = kEmitWarps * 32;
+constexpr int kEmitSlices = kEmitThreads;  // the range totals are summed in this many slices
+struct alignas(16) EmitSmem {
+    uint32_t spre[kEmitWarps][32 * 8];   // [lane * 8 + k]: hits before segment k of the lane's
+                                         // stage, in lists | all << 16
+    uint32_t soff[kEmitWarps][32 * 8];   // its pool entry (kNone: none)
+    alignas(16) uint16_t estage[kEmitWarps][32 * 16];  // staging of a mask segment's offsets
+    uint32_t scan_tmp[kEmitWarps];
+    uint64_t batch_excl[kEmitThreads];
+    uint64_t slice_pre[kEmitSlices];     // exclusive prefix of the slices' range totals
+    uint64_t range_base;                 // output offset of the claimed range
+    uint32_t claim;
 };
 
 // Window hashes: the head slot is the top 12 bits, the tag bits 4..19 (never 0).
@@ -194,6 +220,14 @@ __global__ void build_group_tables_kernel(const Params P) {
     for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < H.nranges; r += gridDim.x * blockDim.x)
         P.range_total[r] = 0ull;
     if (blockIdx.x == 0 && threadIdx.x == 0) *P.pool_ctr = 0u;
+    // segment counts start at zero: phase 1 writes only segments with hits
+    {
+        uint4 *sc = reinterpret_cast<uint4 *>(P.seg_count);  // 8 counts (two uint4) per stage
+        const uint64_t nv = H.jstages * (kConsumerWarps / 4);
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv;
+             i += (uint64_t)gridDim.x * blockDim.x)
+            sc[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
     // block-variant tables, one block per job
     for (uint32_t j = blockIdx.x; j < H.njobs; j += gridDim.x) {
         const JobDesc &D = P.jobs[j];
@@ -218,12 +252,13 @@ __global__ void build_group_tables_kernel(const Params P) {
     for (uint32_t g = blockIdx.x; g < H.ngroups; g += gridDim.x) {
         const GroupDesc &G = H.groups[g];
         if (G.comb == kNone) continue;
-        SharedTable &T = P.comb[G.comb];  // (groups of more than one pattern)
+        SharedTable &T = P.comb[G.comb].t;  // (groups of more than one pattern)
+        uint32_t (*tpw)[8] = P.comb[G.comb].pw;
         for (int i = threadIdx.x; i < kSlots; i += blockDim.x) T.head[i] = 0u;
         for (uint32_t i = threadIdx.x; i < G.nshared; i += blockDim.x) {
             const JobDesc &D = P.jobs[H.group_jobs[G.job0 + i]];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) T.pw[i][k] = D.job.pat.w[k];
+            for (int k = 0; k < 8; ++k) tpw[i][k] = D.job.pat.w[k];
             T.stage0[i] = D.stage0;
             T.nst[i] = (uint32_t)D.nstages;
             T.m[i] = D.job.pat.m;
@@ -251,14 +286,14 @@ __global__ void build_group_tables_kernel(const Params P) {
             const uint32_t lk = (uint32_t)(__ffs((int)D.kstride) - 1);
             const uint32_t e = D.ent0 + j;
             const uint32_t old = atomicExch(&T.head[slot_of(x)], (tag_of(x) << 16) | (e + 1u));
-            T.ent[e] = make_uint4(lo, hi, (i << 8) | ((w4 ? 1u : 0u) << 7) | (lk << 4) | j,
-                                  old ? (old & 0xFFFFu) - 1u : kEndChain);
+            const uint32_t next = old ? (old & 0xFFFFu) - 1u : kEndChain;
+            T.ent[e] = make_uint2(lo, next | (j << 11) | (lk << 14) | ((w4 ? 1u : 0u) << 16) | (i << 17));
         }
         __syncthreads();
         // a slot holding a chain of several entries gets tag 0 (always walk it)
         for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
             const uint32_t v = T.head[i];
-            if (v && T.ent[(v & 0xFFFFu) - 1u].w != kEndChain) T.head[i] = v & 0xFFFFu;
+            if (v && (T.ent[(v & 0xFFFFu) - 1u].y & kEndChain) != kEndChain) T.head[i] = v & 0xFFFFu;
         }
         __syncthreads();
     }
@@ -343,14 +378,48 @@ __device__ __forceinline__ void producer(const Params &P, const Header &H, Smem 
     for (uint32_t i = lo; i < issued; ++i) mbar_wait(&S.full[i % kRing], (i / kRing) & 1);
 }
 
-// Phase-1 result of one pattern segment (a whole warp; lane l holds the hit
-// masks of chunks 32u + l): the count, added to its emit range's total, and,
-// when positions are wanted, the sorted list of hit offsets in the segment
-// (chunk * 16 + bit) in the warp's current pool chunk.
+// Pool entries for one segment: the warp's current chunk, or a new one
+// (lane 0; kNone when the pool is exhausted).  align: 1, or 4 for masks.
+__device__ __forceinline__ uint32_t pool_take(const Params &P, const Header &H, Smem &S, int w,
+                                              uint32_t n, uint32_t align) {
+    uint32_t cur = (S.pcur[w] + align - 1u) & ~(align - 1u);
+    if (cur + n > S.pend[w]) {
+        const uint32_t b = atomicAdd(P.pool_ctr, kPoolChunk);
+        cur = b;
+        S.pend[w] = (uint64_t)b + kPoolChunk <= H.pool_cap ? b + kPoolChunk : b;
+    }
+    if (cur + n > S.pend[w]) {
+        S.pcur[w] = cur;
+        set_err(P.err, kErrCapacity);
+        return kNone;
+    }
+    S.pcur[w] = cur + n;
+    return cur;
+}
+
 __device__ __noinline__ void store_list_emit(const Params &P, const Header &H, Smem &S, uint64_t st,
                                              uint64_t seg, uint32_t h0, uint32_t h1, uint32_t h2,
                                              uint32_t h3, int w, int lane) {
     const uint32_t h[4] = {h0, h1, h2, h3};
+    const uint32_t total = warp_sum(__popc(h0) + __popc(h1) + __popc(h2) + __popc(h3));
+    if (total >= kMaskMin) {
+        // many hits: the 128 chunk masks, lane-major (lane l: chunks l, 32+l,
+        // 64+l, 96+l as one 8-byte word)
+        uint32_t base = 0u;
+        if (lane == 0) {
+            P.seg_count[seg] = total;
+            atomicAdd(&P.range_total[st / H.range_stages], (unsigned long long)total);
+            base = pool_take(P, H, S, w, kSegChunks, 4u);
+            P.seg_off[seg] = base == kNone ? kNone : (base | kMaskFlag);
+        }
+        base = __shfl_sync(kFull, base, 0);
+        if (base == kNone) return;
+        uint2 packed;
+        packed.x = (h0 & 0xFFFFu) | (h1 << 16);
+        packed.y = (h2 & 0xFFFFu) | (h3 << 16);
+        reinterpret_cast<uint2 *>(P.pool + base)[lane] = packed;
+        return;
+    }
     uint32_t c[4], inc[4], T[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -367,23 +436,11 @@ __device__ __noinline__ void store_list_emit(const Params &P, const Header &H, S
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) T[u] = __shfl_sync(kFull, inc[u], 31);
-    const uint32_t total = T[0] + T[1] + T[2] + T[3];
     uint32_t base = 0u;
     if (lane == 0) {
         P.seg_count[seg] = total;
         atomicAdd(&P.range_total[st / H.range_stages], (unsigned long long)total);
-        if (S.pcur[w] + total > S.pend[w]) {
-            const uint32_t b = atomicAdd(P.pool_ctr, kPoolChunk);
-            S.pcur[w] = b;
-            S.pend[w] = (uint64_t)b + kPoolChunk <= H.pool_cap ? b + kPoolChunk : b;
-        }
-        if (S.pcur[w] + total <= S.pend[w]) {
-            base = S.pcur[w];
-            S.pcur[w] += total;
-        } else {
-            base = kNone;  // pool exhausted: no positions for this segment
-            atomicOr(P.err, kErrCapacity);
-        }
+        base = pool_take(P, H, S, w, total, 1u);
         P.seg_off[seg] = base;
     }
     base = __shfl_sync(kFull, base, 0);
@@ -411,16 +468,14 @@ __device__ __noinline__ void store_list_emit(const Params &P, const Header &H, S
 
 // Phase-1 result of one pattern segment (a whole warp; lane l holds the hit
 // masks of chunks 32u + l): the count, added to its emit range's total, and,
-// when positions are wanted, the sorted list of hit offsets in the segment
-// (chunk * 16 + bit) in the warp's current pool chunk (out of line).
+// when positions are wanted, in the warp's current pool chunk either the
+// sorted list of hit offsets in the segment (chunk * 16 + bit) or, for a
+// segment with at least kMaskMin hits, its 128 chunk masks (out of line).
 __device__ __forceinline__ void store_list(const Params &P, const Header &H, Smem &S, uint64_t st,
                                            uint64_t seg, uint32_t h0, uint32_t h1, uint32_t h2,
                                            uint32_t h3, int w, int lane) {
-    const uint32_t any = __any_sync(kFull, (h0 | h1 | h2 | h3) != 0u);
-    if (!any) {
-        if (lane == 0) P.seg_count[seg] = 0u;
-        return;
-    }
+    // segments without hits keep the zero count the table kernel wrote
+    if (!__any_sync(kFull, (h0 | h1 | h2 | h3) != 0u)) return;
     if (H.emit) {
         store_list_emit(P, H, S, st, seg, h0, h1, h2, h3, w, lane);
         return;
@@ -524,20 +579,22 @@ __device__ __noinline__ void walk_chains(Smem &S, int w, uint4 cur, uint32_t n0,
             const uint32_t hi = w4 ? 0u : __funnelshift_r(r1, k + 2u <= 5u ? pick_word(cur, n0, n1, k + 2u) : 0u, sh);
             const uint32_t x = w4 ? hash4(lo) : hash8(lo, hi);
             uint32_t e = (S.tab.head[slot_of(x)] & 0xFFFFu) - 1u;
+            (void)hi;  // an 8-byte window is told apart by its tag; the full check decides
             for (int guard = 0; guard < kMaxEnt && e < (uint32_t)kMaxEnt; ++guard) {
-                const uint4 E = S.tab.ent[e];
-                const uint32_t meta = E.z;
-                const uint32_t i = meta >> 8, j = meta & 7u, K = 1u << ((meta >> 4) & 3u);
-                if (((meta >> 7) & 1u) == w4 && E.x == lo && (w4 || E.y == hi) &&
-                    (q & (K - 1u)) == 0u && j <= q && q - j <= 15u) {
+                const uint2 E = S.tab.ent[e];
+                const uint32_t meta = E.y;
+                const uint32_t i = meta >> 17, j = (meta >> 11) & 7u, K = 1u << ((meta >> 14) & 3u);
+                if (((meta >> 16) & 1u) == w4 && E.x == lo && (q & (K - 1u)) == 0u && j <= q &&
+                    q - j <= 15u) {
                     const uint32_t b = q - j;
                     const int64_t Pp = p0 + (int64_t)b;
                     const uint32_t m = S.tab.m[i];
-                    if (Pp >= V.delta && Pp <= V.lim - (int64_t)m && verify_at(S.tab.pw[i], m, Pp, V))
+                    if (Pp >= V.delta && Pp <= V.lim - (int64_t)m && verify_at(V.gpw + 8u * i, m, Pp, V))
                         push_hit(S, w, i, chunk, b);
                 }
-                if (E.w == kEndChain) break;
-                e = E.w;
+                const uint32_t next = meta & kEndChain;
+                if (next == kEndChain) break;
+                e = next;
             }
         }
     }
@@ -584,7 +641,7 @@ __device__ __forceinline__ void filter_chunk(Smem &S, int w, uint4 cur, uint32_t
 __device__ __noinline__ void pattern_pass(const Params &P, const Header &H, const GroupDesc &G,
                                           Smem &S, uint32_t i, uint64_t ls, int w, int lane) {
     const VCtx &V = S.vc[w];
-    const uint32_t *pw = S.tab.pw[i];
+    const uint32_t *pw = V.gpw + 8u * i;
     const uint32_t m = S.tab.m[i];
     const uint64_t c0 = ls * kStageChunks;
     uint4 ch[4];
@@ -632,14 +689,12 @@ __device__ __forceinline__ void finish_shared(const Params &P, const Header &H, 
                                               Smem &S, uint64_t ls, int w, int lane) {
     const uint32_t nS = G.nshared;
     const uint32_t nh = S.nhits[w] < (uint32_t)kHitCap ? S.nhits[w] : (uint32_t)kHitCap;
-    uint32_t *mbuf = S.mbuf[w];
+    uint32_t *mbuf = reinterpret_cast<uint32_t *>(S.stage16[w]);  // 128 chunk masks
     for (uint32_t i0 = 0; i0 < nS; i0 += 32) {
         const uint32_t i = i0 + (uint32_t)lane;
         const bool valid = i < nS && ls < S.tab.nst[i < nS ? i : 0];
         const bool over = valid && ((S.ovf[w][i >> 5] >> (i & 31u)) & 1u);
         const uint32_t hc = valid ? S.hitcnt[w][i] : 0u;
-        if (valid && !over && hc == 0u)
-            P.seg_count[(S.tab.stage0[i] + ls) * kConsumerWarps + (uint64_t)w] = 0u;
         uint32_t todo = __ballot_sync(kFull, valid && !over && hc != 0u);
         while (todo) {
             const uint32_t ii = i0 + (uint32_t)(__ffs(todo) - 1);
@@ -684,6 +739,7 @@ __device__ __noinline__ void shared_filter(const Params &P, const Header &H, con
         V.lim = (int64_t)G.text.lim;
         V.sbase = (int64_t)(c0 * 16u);
         V.inside = (c0 >= G.chunk_full0 && c0 + kStageChunks + 1u <= G.chunk_full1) ? 1u : 0u;
+        V.gpw = &P.comb[G.comb].pw[0][0];
     }
     if (lane < kMaxShared / 32) S.ovf[w][lane] = 0u;
     for (uint32_t i = lane; i < (G.nshared + 1u) / 2u; i += 32)
@@ -794,7 +850,7 @@ __device__ __forceinline__ void consumer(const Params &P, const Header &H, Smem 
         if (G.comb != kNone && tab_group != g) {
             if (lane == 0) mbar_arrive(&S.tab_free);
             if (!warp_wait(&S.tab_free, tab_loads & 1u)) { *ok = false; break; }
-            const uint4 *src = reinterpret_cast<const uint4 *>(&P.comb[G.comb]);
+            const uint4 *src = reinterpret_cast<const uint4 *>(&P.comb[G.comb].t);
             uint4 *dst = reinterpret_cast<uint4 *>(&S.tab);
             for (int i = t; i < (int)(sizeof(SharedTable) / 16); i += kConsumerWarps * 32) dst[i] = src[i];
             __syncwarp();
@@ -831,77 +887,178 @@ __device__ __forceinline__ uint32_t first_job_from(const JobDesc *jobs, uint32_t
     return lo;
 }
 
-// Emission of the pattern stages [st0, st1) with output offset base0:
-// batches of 256 segments, a block scan of their counts, then each warp
-// copies the hit lists of its 32 segments as one flat sequence (lane q takes
-// hits q, q + 32, ...; the segment of a hit is found by a binary search over
-// the warp's inclusive counts), so the stores of a warp are consecutive.
-__device__ __forceinline__ void emit_range(const Params &P, const Header &H, Smem &S, uint64_t st0,
+// Emission of the pattern stages [st0, st1) with output offset base0, in
+// batches of 256 stages (one per consumer thread: its 8 segment counts, one
+// block scan of the stage totals; the next batch's counts are loaded before
+// this one is processed).  Each warp then copies the hit lists of its 32
+// stages as one flat sequence: lane q takes hits q, q + 32, .. of it, finds
+// the stage (binary search over the warp's inclusive totals) and the segment
+// (the stage's 8 prefix counts, in shared memory), and writes segment start +
+// offset; consecutive lanes store consecutive positions and the pool loads of
+// many stages overlap.  The per-warp phase-1 buffers hold the stages' segment
+// prefixes and list offsets here.
+__device__ __forceinline__ void emit_range(const Params &P, const Header &H, EmitSmem &S, uint64_t st0,
                                            uint64_t st1, uint64_t base0, int w, int lane) {
     const int t = w * 32 + lane;
-    const uint64_t seg0 = st0 * kConsumerWarps, seg1 = st1 * kConsumerWarps;
     uint64_t base = base0;
     uint32_t jcur = first_job_from(P.jobs, H.njobs, st0);
     uint32_t wj = jcur > 0 ? jcur - 1u : 0u;
-    for (uint64_t sb = seg0; sb < seg1; sb += kConsumerWarps * 32) {
-        const uint64_t seg = sb + (uint64_t)t;
-        const uint32_t c = seg < seg1 ? P.seg_count[seg] : 0u;
+    const uint4 *sc = reinterpret_cast<const uint4 *>(P.seg_count);
+    uint32_t *spre = S.spre[w];
+    uint32_t *soff = S.soff[w];
+    uint16_t *estage = S.estage[w];
+    uint4 na = make_uint4(0u, 0u, 0u, 0u), nb = na;
+    if (st0 + (uint64_t)t < st1) {
+        na = sc[2 * (st0 + (uint64_t)t)];
+        nb = sc[2 * (st0 + (uint64_t)t) + 1];
+    }
+    for (uint64_t sb = st0; sb < st1; sb += kEmitThreads) {
+        const uint64_t stg = sb + (uint64_t)t;
+        const uint4 ca = na, cb = nb;
+        const uint64_t nx = stg + kEmitThreads;
+        na = nb = make_uint4(0u, 0u, 0u, 0u);  // past the range: no stage
+        if (nx < st1) {
+            na = sc[2 * nx];
+            nb = sc[2 * nx + 1];
+        }
+        const uint32_t c = ca.x + ca.y + ca.z + ca.w + cb.x + cb.y + cb.z + cb.w;
         const uint32_t inc = warp_incl_scan(c, lane);
         if (lane == 31) S.scan_tmp[w] = inc;
-        consumer_sync();
+        __syncthreads();
         uint32_t wbase = 0u, btotal = 0u;
 #pragma unroll
-        for (int k = 0; k < kConsumerWarps; ++k) {
+        for (int k = 0; k < kEmitWarps; ++k) {
             const uint32_t v = S.scan_tmp[k];
             if (k < w) wbase += v;
             btotal += v;
         }
         const uint64_t excl = base + wbase + inc - c;
         S.batch_excl[t] = excl;
-        consumer_sync();
+        __syncthreads();
         if (t == 0) {
-            const uint64_t bst1 = (sb + kConsumerWarps * 32) / kConsumerWarps;
+            const uint64_t bst1 = sb + kEmitThreads;
             while (jcur < H.njobs && P.jobs[jcur].stage0 < bst1 && P.jobs[jcur].stage0 < st1) {
-                P.offsets[jcur] = S.batch_excl[P.jobs[jcur].stage0 * kConsumerWarps - sb];
+                P.offsets[jcur] = S.batch_excl[P.jobs[jcur].stage0 - sb];
                 ++jcur;
             }
         }
         const uint32_t wtotal = __shfl_sync(kFull, inc, 31);
-        if (wtotal != 0u && H.emit) {
-            // this lane's segment: pool list and start of its first chunk
-            uint32_t off = 0u;
+        if (H.emit && wtotal != 0u) {
+            // this lane's stage: start, and per segment k its list offset and
+            // the numbers of hits before it in the stage (all / in lists)
             int64_t s0 = 0;
+            uint32_t lcount = 0u;    // hits of the stage held in lists
+            uint32_t mbits = 0u;     // segments held as masks
             if (c != 0u) {
-                off = P.seg_off[seg];
-                const uint64_t stg = seg / kConsumerWarps;
                 while (wj + 1u < H.njobs && P.jobs[wj + 1u].stage0 <= stg) ++wj;
                 const JobDesc &D = P.jobs[wj];
-                s0 = (int64_t)(((stg - D.stage0) * kStageChunks + (seg % kConsumerWarps) * kSegChunks) * 16u) +
-                     D.off - (int64_t)D.job.delta;
+                s0 = (int64_t)((stg - D.stage0) * (uint64_t)kStageBytes) + D.off - (int64_t)D.job.delta;
+                const uint4 oa = reinterpret_cast<const uint4 *>(P.seg_off)[2 * stg];
+                const uint4 ob = reinterpret_cast<const uint4 *>(P.seg_off)[2 * stg + 1];
+                const uint32_t cs[8] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+                const uint32_t os[8] = {oa.x, oa.y, oa.z, oa.w, ob.x, ob.y, ob.z, ob.w};
+                uint32_t all = 0u;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t o = cs[k] ? os[k] : kNone;
+                    const bool mk = o != kNone && (o & kMaskFlag);
+                    spre[lane * 8 + k] = lcount | (all << 16);
+                    soff[lane * 8 + k] = o;
+                    if (mk) mbits |= 1u << k;
+                    else if (o != kNone) lcount += cs[k];  // (kNone: no pool room, not emitted)
+                    all += cs[k];
+                }
             }
+            __syncwarp();
             const uint64_t wexcl = __shfl_sync(kFull, excl, 0);
-            if (lane == 0 && wexcl + wtotal > H.capacity) atomicOr(P.err, kErrCapacity);
-            for (uint32_t q0 = 0; q0 < wtotal; q0 += 32u) {
+            if (lane == 0 && wexcl + wtotal > H.capacity) set_err(P.err, kErrCapacity);
+            const uint16_t *__restrict__ pool = P.pool;
+            uint64_t *__restrict__ out = H.positions;
+            // segments held as masks: expanded a segment at a time (staged in
+            // the table's shared memory, which phase 3 no longer needs)
+            uint32_t todo = __ballot_sync(kFull, mbits != 0u);
+            while (todo) {
+                const int j = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                uint32_t mb = __shfl_sync(kFull, mbits, j);
+                const uint64_t ej = __shfl_sync(kFull, excl, j);
+                const int64_t sj = __shfl_sync(kFull, s0, j);
+                while (mb) {
+                    // the masks of up to four segments are loaded together
+                    uint32_t ks[4];
+                    uint2 pk4[4];
+                    int nk = 0;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        ks[r] = 8u;
+                        if (mb) {
+                            ks[r] = (uint32_t)(__ffs(mb) - 1);
+                            mb &= mb - 1u;
+                            const uint32_t o = soff[j * 8 + ks[r]] & ~kMaskFlag;
+                            pk4[r] = reinterpret_cast<const uint2 *>(pool + o)[lane];
+                            nk = r + 1;
+                        }
+                    }
+#pragma unroll 1
+                    for (int r = 0; r < nk; ++r) {
+                        uint32_t k = ks[0];
+                        uint2 packed = pk4[0];
+#pragma unroll
+                        for (int q = 1; q < 4; ++q)
+                            if (q == r) {
+                                k = ks[q];
+                                packed = pk4[q];
+                            }
+                        const uint32_t pk = spre[j * 8 + k] >> 16;
+                        emit_segment(out, H.capacity, P.err, sj + (int64_t)(k * (uint32_t)(kSegChunks * 16)),
+                                     ej + pk, packed, estage, lane);
+                    }
+                }
+            }
+            // hits held in lists: one flat sequence across the warp, lane q
+            // taking hits q, q + 32, ..
+            const uint32_t incs = warp_incl_scan(lcount, lane);
+            const uint32_t stotal = __shfl_sync(kFull, incs, 31);
+            for (uint32_t q0 = 0; q0 < stotal; q0 += 32u) {
                 const uint32_t q = q0 + (uint32_t)lane;
-                // segment j: the first lane whose inclusive count exceeds q
                 uint32_t j = 0u;
 #pragma unroll
                 for (int d = 16; d > 0; d >>= 1) {
-                    const uint32_t v = __shfl_sync(kFull, inc, (int)(j + (uint32_t)d - 1u));
+                    const uint32_t v = __shfl_sync(kFull, incs, (int)(j + (uint32_t)d - 1u));
                     if (v <= q) j += (uint32_t)d;
                 }
                 j = j < 31u ? j : 31u;
-                const uint32_t ij = __shfl_sync(kFull, inc, (int)j);
-                const uint32_t cj = __shfl_sync(kFull, c, (int)j);
-                const uint32_t oj = __shfl_sync(kFull, off, (int)j);
+                const uint32_t ij = __shfl_sync(kFull, incs, (int)j);
+                const uint32_t cj = __shfl_sync(kFull, lcount, (int)j);
+                const uint64_t ej = __shfl_sync(kFull, excl, (int)j);
                 const int64_t sj = __shfl_sync(kFull, s0, (int)j);
-                const uint64_t idx = wexcl + q;
-                if (q < wtotal && oj != kNone && idx < H.capacity)
-                    H.positions[idx] = (uint64_t)(sj + (int64_t)P.pool[oj + (q - (ij - cj))]);
+                if (q < stotal) {
+                    const uint32_t within = q - (ij - cj);  // among the stage's list hits
+                    const uint32_t *pr = spre + j * 8u;
+                    uint32_t k = 0u, pv = pr[0];
+#pragma unroll
+                    for (int kk = 1; kk < 8; ++kk) {
+                        const uint32_t v = pr[kk];
+                        // a later list segment that starts at or before `within`
+                        // (mask segments and empty ones do not advance the list count)
+                        if ((v & 0xFFFFu) <= within && soff[j * 8u + kk] != kNone &&
+                            !(soff[j * 8u + kk] & kMaskFlag)) {
+                            k = (uint32_t)kk;
+                            pv = v;
+                        }
+                    }
+                    const uint32_t ok_ = soff[j * 8u + k];
+                    const uint32_t inlist = within - (pv & 0xFFFFu);
+                    const uint64_t idx = ej + (pv >> 16) + inlist;
+                    if (ok_ != kNone && idx < H.capacity)
+                        out[idx] = (uint64_t)(sj + (int64_t)(k * (uint32_t)(kSegChunks * 16)) +
+                                              (int64_t)pool[ok_ + inlist]);
+                }
             }
+            __syncwarp();
         }
         base += btotal;
-        consumer_sync();
+        __syncthreads();
     }
 }
 
@@ -937,63 +1094,81 @@ __global__ void __launch_bounds__(stream::kThreadsStream, stream::kMaxBlocksPerS
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0 && !grid_barrier(P.misc)) atomicOr(P.err, kErrTimeout);
-    __syncthreads();
-
-    // phase 2: block b emits ranges b, b + grid, b + 2 grid, ...  Each block
-    // takes the exclusive prefix of all range totals: consumer thread t sums a
-    // slice of them, one block scan over the slices, and the owner of a slice
-    // holding one of the block's ranges adds the slice's part before it.
-    const uint32_t nr = H.nranges, G = gridDim.x, b = blockIdx.x;
-    if (warp < kConsumerWarps) {
-        const int t = warp * 32 + lane;
-        const uint32_t per = (nr + kConsumerWarps * 32 - 1) / (kConsumerWarps * 32);
-        const uint32_t r0 = (uint32_t)t * per, r1 = r0 + per < nr ? r0 + per : nr;
-        const uint64_t *rt = reinterpret_cast<const uint64_t *>(P.range_total);
-        uint64_t sum = 0;
-        for (uint32_t r = r0; r < r1; ++r) sum += ld_relaxed_u64(rt + r);
-        uint64_t inc = sum;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint64_t v = __shfl_up_sync(kFull, inc, d);
-            if (lane >= d) inc += v;
-        }
-        if (lane == 31) S.scan_tmp64[warp] = inc;
-        consumer_sync();
-        uint64_t before = 0, all = 0;
-#pragma unroll
-        for (int k = 0; k < kConsumerWarps; ++k) {
-            const uint64_t v = S.scan_tmp64[k];
-            if (k < warp) before += v;
-            all += v;
-        }
-        uint64_t run = before + inc - sum;
-        for (uint32_t r = r0; r < r1; ++r) {
-            if (r % G == b) S.range_excl[r / G] = run;
-            run += ld_relaxed_u64(rt + r);
-        }
-        if (t == 0) {
-            S.total = all;
-            if (b == 0) P.offsets[H.njobs] = all;
-        }
-    }
-    __syncthreads();
-    // phase 3
-    if (warp < kConsumerWarps && H.njobs > 0) {
-        for (uint32_t r = b, k = 0; r < nr; r += G, ++k) {
-            const uint64_t st0 = (uint64_t)r * H.range_stages;
-            const uint64_t st1 = st0 + H.range_stages < H.jstages ? st0 + H.range_stages : H.jstages;
-            if (st0 < st1) emit_range(P, H, S, st0, st1, S.range_excl[k], warp, lane);
-        }
-    }
-    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         const uint32_t d = atomicAdd(&P.misc->done, 1u);
         if (d == gridDim.x - 1u) {
             P.misc->ticket = 0u;
             P.misc->done = 0u;
-            P.misc->barrier = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// Emission of a batched search (after group_kernel): the pattern stages are
+// cut into ranges whose hit totals group_kernel accumulated; blocks claim
+// ranges dynamically (dense ranges take longer than sparse ones), and each
+// block first takes the exclusive prefix of all range totals in 256 slices
+// (one per thread, one block scan) so that a claimed range's output offset is
+// its slice's prefix plus the totals before it in the slice.
+__global__ void __launch_bounds__(group::kEmitThreads, 4)
+    group_emit_kernel(const __grid_constant__ group::Params P) {
+    using namespace group;
+    __shared__ EmitSmem S;
+    const Header H = *P.hdr;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const uint32_t nr = H.nranges;
+    const uint32_t per = (nr + kEmitSlices - 1) / kEmitSlices;
+    const uint64_t *rt = reinterpret_cast<const uint64_t *>(P.range_total);
+    {
+        const uint32_t r0 = (uint32_t)t * per, r1 = r0 + per < nr ? r0 + per : nr;
+        uint64_t sum = 0;
+#pragma unroll 8
+        for (uint32_t r = r0; r < r1; ++r) sum += rt[r];
+        uint64_t inc = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint64_t v = __shfl_up_sync(kFull, inc, d);
+            if (lane >= d) inc += v;
+        }
+        if (lane == 31) S.batch_excl[warp] = inc;
+        __syncthreads();
+        uint64_t before = 0, all = 0;
+#pragma unroll
+        for (int k = 0; k < kEmitWarps; ++k) {
+            const uint64_t v = S.batch_excl[k];
+            if (k < warp) before += v;
+            all += v;
+        }
+        S.slice_pre[t] = before + inc - sum;
+        if (t == 0 && blockIdx.x == 0) P.offsets[H.njobs] = all;
+        __syncthreads();
+    }
+    for (;;) {
+        if (t == 0) S.claim = atomicAdd(&P.misc->ticket2, 1u);
+        __syncthreads();
+        const uint32_t r = S.claim;
+        if (r >= nr || H.njobs == 0) break;
+        if (warp == 0) {
+            // output offset of range r: its slice's prefix + the totals before r
+            const uint32_t sl = r / per;
+            uint64_t part = 0;
+            for (uint32_t q = sl * per + (uint32_t)lane; q < r; q += 32) part += rt[q];
+            part = warp_sum64(part);
+            if (lane == 0) S.range_base = S.slice_pre[sl] + part;
+        }
+        __syncthreads();
+        const uint64_t st0 = (uint64_t)r * H.range_stages;
+        const uint64_t st1 = st0 + H.range_stages < H.jstages ? st0 + H.range_stages : H.jstages;
+        if (st0 < st1) emit_range(P, H, S, st0, st1, S.range_base, warp, lane);
+        __syncthreads();
+    }
+    if (t == 0) {
+        __threadfence();
+        const uint32_t d = atomicAdd(&P.misc->done2, 1u);
+        if (d == gridDim.x - 1u) {
+            P.misc->ticket2 = 0u;
+            P.misc->done2 = 0u;
             __threadfence();
         }
     }

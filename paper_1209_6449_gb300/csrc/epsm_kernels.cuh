@@ -15,6 +15,8 @@ struct DevMisc {
     uint32_t done;     // blocks that have finished
     uint32_t err;      // device error bits
     uint32_t barrier;  // arrivals at the streaming kernel's grid barrier
+    uint32_t ticket2;  // next emit range to claim (batched emission kernel)
+    uint32_t done2;    // emission blocks that have finished
 };
 
 __device__ __forceinline__ uint32_t claim_tile(DevMisc *misc) { return atomicAdd(&misc->ticket, 1u); }

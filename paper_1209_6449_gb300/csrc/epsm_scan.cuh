@@ -117,6 +117,14 @@ __device__ __forceinline__ uint32_t load_word(const SearchJob &J, uint64_t widx)
     return w;
 }
 
+// Sets an error bit; reads first so that many reporters of the same
+// condition do not all queue an atomic on one word.
+__device__ __forceinline__ void set_err(uint32_t *err, uint32_t bit) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(err) : "memory");
+    if (!(v & bit)) atomicOr(err, bit);
+}
+
 // ---------------------------------------------------------------------------
 // packed-byte helpers (the wscmp idea of Section 3.1 on 32-bit lanes)
 // ---------------------------------------------------------------------------

@@ -346,7 +346,7 @@ __device__ __forceinline__ void emit_segment(uint64_t *positions, uint64_t capac
 #pragma unroll
     for (int u = 0; u < 4; ++u) T[u] = __shfl_sync(kFull, inc[u], 31);
     const uint32_t total = T[0] + T[1] + T[2] + T[3];
-    if (lane == 0 && idx0 + total > capacity) atomicOr(err, kErrCapacity);
+    if (lane == 0 && idx0 + total > capacity) set_err(err, kErrCapacity);
     if (total <= 32u * 16u) {
         uint32_t before = 0u;
 #pragma unroll
