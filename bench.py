@@ -64,6 +64,13 @@ def parse():
                          "launches an ncu traffic capture measures")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-pairs", type=int, default=8192)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-rates", default="2000,10000,50000",
+                    help="Poisson arrival rates (queries/s) of the served workload")
+    ap.add_argument("--serve-secs", type=float, default=1.0,
+                    help="arrival window per rate for the serving engine")
+    ap.add_argument("--serve-pq-secs", type=float, default=0.25,
+                    help="arrival window per rate for the per-query path (it saturates early)")
     return ap.parse_args()
 
 
@@ -484,6 +491,10 @@ def main():
         del texts, out
         torch.cuda.empty_cache()
         batched = run_batched(ctx, torch, args.batch_pairs)
+    served = None
+    if not args.no_serve and world == 1:
+        torch.cuda.empty_cache()
+        served = run_served(torch, args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
@@ -501,6 +512,7 @@ def main():
                 "cpu_baseline": cpu,
                 "e2e": e2e,
                 "batched": batched,
+                "served": served,
                 "gpu_launches": launches,
                 "clocks": clocks.summary(t_wall0, t_wall1),
                 "occurrences_per_step": occ_total}
@@ -509,6 +521,87 @@ def main():
         dist.destroy_process_group()
     ctx.close()
     return 0
+
+
+def run_served(torch, args):
+    """The served workload: 4 corpora of 1 GiB resident in HBM (sigma 4, 20,
+    64 Zipf, 96-symbol order-2 Markov), a Poisson stream of queries (corpus
+    uniform, pattern from a pool of 1024 per corpus with m uniform in 2..32,
+    half copied from the corpus, half i.i.d.), 1% of requests uploading a new
+    16..256 MiB text (admitted against a 16 GiB upload budget, least recently
+    used uploads evicted).  Each rate is replayed through the serving engine
+    (continuous batching, two launches in flight) and through the per-query
+    path (one single-search launch per query); latency = result published -
+    scheduled arrival."""
+    import gen
+    import paper_1209_6449_gb300 as epsm
+    n = 1 << 30
+    kinds = ("dna", "protein", "nl64", "markov96")
+    stream = torch.cuda.current_stream().cuda_stream
+    bufs, specs = [], []
+    for i, k in enumerate(kinds):
+        b = torch.empty(n + 16, dtype=torch.uint8, device="cuda")
+        sp = gen.TextSpec(k, 900 + i)
+        sp.device(n, b.data_ptr(), stream)
+        bufs.append(b)
+        specs.append(sp)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(7)
+    pool = []
+    for c, sp in enumerate(specs):
+        for k in range(1024):
+            m = int(rng.integers(2, 33))
+            p = (gen.planted_patterns(sp, n, m, 1, stream_seed=k)[0] if k % 2
+                 else gen.random_patterns(sp, m, 1, stream_seed=k)[0])
+            pool.append((c, p))
+    uploads = [gen.TextSpec("protein", 77).host(u) for u in (16 << 20, 64 << 20, 128 << 20, 256 << 20)]
+
+    def stream_for(rate, secs, seed):
+        r = np.random.default_rng(seed)
+        cnt = int(rate * secs)
+        at = np.cumsum(r.exponential(1e9 / rate, size=cnt)).astype(np.int64)
+        kind = (r.random(cnt) < 0.01).astype(np.uint32)
+        idx = r.integers(0, len(pool), size=cnt)
+        corp = np.array([pool[i][0] for i in idx], dtype=np.uint32)
+        pay = [uploads[int(r.integers(0, 4))] if kind[j] else pool[idx[j]][1] for j in range(cnt)]
+        return at, kind, corp, pay
+
+    def replay(per_query, rate, secs):
+        srv = epsm.Server(0, max_batch=1024, inflight=2, per_query=per_query,
+                          upload_budget=16 << 30, out_capacity=1 << 29)
+        for b in bufs:
+            srv.add_corpus((b.data_ptr(), n))
+        at, kind, corp, pay = stream_for(rate, args.serve_secs, 11)
+        cnt = int(rate * secs)
+        res = srv.replay(at[:cnt], kind[:cnt], corp[:cnt], pay[:cnt])
+        stats = srv.stats()
+        srv.close()
+        q = kind[:cnt] == 0
+        lat = res["latency_ns"][q] / 1e6
+        return ({"offered_qps": rate, "queries": int(q.sum()), "uploads": int((~q).sum()),
+                 "qps": round(float(q.sum()) / res["elapsed_s"], 1),
+                 "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                 "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                 "all_ok": bool((res["status"] == 0).all()),
+                 "batches": stats["batches"], "evictions": stats["evictions"]},
+                res["counts"])
+
+    out = []
+    for rate in [int(x) for x in args.serve_rates.split(",")]:
+        srv, c1 = replay(False, rate, args.serve_secs)
+        pq, c2 = replay(True, rate, min(args.serve_secs, args.serve_pq_secs))
+        out.append({"served": srv, "per_query": pq,
+                    "same_counts": bool((c1[:len(c2)] == c2).all()),
+                    "qps_ratio": round(srv["qps"] / pq["qps"], 2)})
+    del bufs
+    torch.cuda.empty_cache()
+    return {"workload": "4 resident 1 GiB corpora (sigma 4, 20, 64 Zipf, 96 order-2 Markov); Poisson "
+                        "queries, m uniform 2..32 from a 1024-pattern pool per corpus (half planted); "
+                        "1% uploads of 16..256 MiB texts under a 16 GiB budget",
+            "engine": "epsm_server (continuous batching, 2 launches in flight, up to 1024 queries "
+                      "per batch) vs per-query (one single-search launch per query)",
+            "latency": "result published - scheduled arrival",
+            "rates": out}
 
 
 def run_e2e(ctx, pats, args, torch, dev, dist):

@@ -397,45 +397,13 @@ __device__ __forceinline__ uint32_t pool_take(const Params &P, const Header &H, 
     return cur;
 }
 
-__device__ __noinline__ void store_list_emit(const Params &P, const Header &H, Smem &S, uint64_t st,
-                                             uint64_t seg, uint32_t h0, uint32_t h1, uint32_t h2,
-                                             uint32_t h3, int w, int lane) {
-    const uint32_t h[4] = {h0, h1, h2, h3};
-    const uint32_t total = warp_sum(__popc(h0) + __popc(h1) + __popc(h2) + __popc(h3));
-    if (total >= kMaskMin) {
-        // many hits: the 128 chunk masks, lane-major (lane l: chunks l, 32+l,
-        // 64+l, 96+l as one 8-byte word)
-        uint32_t base = 0u;
-        if (lane == 0) {
-            P.seg_count[seg] = total;
-            atomicAdd(&P.range_total[st / H.range_stages], (unsigned long long)total);
-            base = pool_take(P, H, S, w, kSegChunks, 4u);
-            P.seg_off[seg] = base == kNone ? kNone : (base | kMaskFlag);
-        }
-        base = __shfl_sync(kFull, base, 0);
-        if (base == kNone) return;
-        uint2 packed;
-        packed.x = (h0 & 0xFFFFu) | (h1 << 16);
-        packed.y = (h2 & 0xFFFFu) | (h3 << 16);
-        reinterpret_cast<uint2 *>(P.pool + base)[lane] = packed;
-        return;
-    }
-    uint32_t c[4], inc[4], T[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        c[u] = __popc(h[u]);
-        inc[u] = c[u];
-    }
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint32_t t = __shfl_up_sync(kFull, inc[u], d);
-            if (lane >= d) inc[u] += t;
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) T[u] = __shfl_sync(kFull, inc[u], 31);
+// The sorted offset list of a segment with few hits (a whole warp): per
+// step u, a warp scan of the lanes' counts, the offsets put in order in
+// shared memory, then stored with consecutive lanes on consecutive entries.
+// Out of line and compact (a rolled loop): it runs for sparse segments only.
+__device__ __noinline__ void store_short_list(const Params &P, const Header &H, Smem &S, uint64_t st,
+                                              uint64_t seg, uint32_t h0, uint32_t h1, uint32_t h2,
+                                              uint32_t h3, uint32_t total, int w, int lane) {
     uint32_t base = 0u;
     if (lane == 0) {
         P.seg_count[seg] = total;
@@ -445,46 +413,57 @@ __device__ __noinline__ void store_list_emit(const Params &P, const Header &H, S
     }
     base = __shfl_sync(kFull, base, 0);
     if (base == kNone) return;
-    // each step's offsets are put in order in shared memory, then stored to
-    // the pool with consecutive lanes on consecutive entries
     uint16_t *stg = S.stage16[w];
-    uint32_t before = 0u;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        if (T[u] == 0u) continue;
-        uint32_t k = inc[u] - c[u];
-        uint32_t hh = h[u];
+#pragma unroll 1
+    for (uint32_t u = 0; u < 4u; ++u) {
+        uint32_t hh = u == 0u ? h0 : (u == 1u ? h1 : (u == 2u ? h2 : h3));
+        const uint32_t c = __popc(hh);
+        const uint32_t inc = warp_incl_scan(c, lane);
+        const uint32_t T = __shfl_sync(kFull, inc, 31);
+        if (T == 0u) continue;
+        uint32_t k = inc - c;
         while (hh) {
             const uint32_t b = (uint32_t)(__ffs(hh) - 1);
             hh &= hh - 1u;
             stg[k++] = (uint16_t)((32u * u + (uint32_t)lane) * 16u + b);
         }
         __syncwarp();
-        for (uint32_t q = (uint32_t)lane; q < T[u]; q += 32u) P.pool[base + before + q] = stg[q];
+        for (uint32_t q = (uint32_t)lane; q < T; q += 32u) P.pool[base + q] = stg[q];
         __syncwarp();
-        before += T[u];
+        base += T;
     }
 }
 
 // Phase-1 result of one pattern segment (a whole warp; lane l holds the hit
 // masks of chunks 32u + l): the count, added to its emit range's total, and,
-// when positions are wanted, in the warp's current pool chunk either the
-// sorted list of hit offsets in the segment (chunk * 16 + bit) or, for a
-// segment with at least kMaskMin hits, its 128 chunk masks (out of line).
+// when positions are wanted, in the warp's current pool chunk either its 128
+// chunk masks (at least kMaskMin hits: lane-major, lane l's four masks as one
+// 8-byte word) or the sorted list of its hit offsets (chunk * 16 + bit).
 __device__ __forceinline__ void store_list(const Params &P, const Header &H, Smem &S, uint64_t st,
                                            uint64_t seg, uint32_t h0, uint32_t h1, uint32_t h2,
                                            uint32_t h3, int w, int lane) {
     // segments without hits keep the zero count the table kernel wrote
-    if (!__any_sync(kFull, (h0 | h1 | h2 | h3) != 0u)) return;
-    if (H.emit) {
-        store_list_emit(P, H, S, st, seg, h0, h1, h2, h3, w, lane);
+    const uint32_t cnt = __popc(h0) + __popc(h1) + __popc(h2) + __popc(h3);
+    if (!__any_sync(kFull, cnt != 0u)) return;
+    const uint32_t total = warp_sum(cnt);
+    if (H.emit && total < kMaskMin) {
+        store_short_list(P, H, S, st, seg, h0, h1, h2, h3, total, w, lane);
         return;
     }
-    const uint32_t total = warp_sum(__popc(h0) + __popc(h1) + __popc(h2) + __popc(h3));
+    uint32_t base = 0u;
     if (lane == 0) {
         P.seg_count[seg] = total;
         atomicAdd(&P.range_total[st / H.range_stages], (unsigned long long)total);
+        if (H.emit) {
+            base = pool_take(P, H, S, w, kSegChunks, 4u);
+            P.seg_off[seg] = base == kNone ? kNone : (base | kMaskFlag);
+        }
     }
+    if (!H.emit) return;
+    base = __shfl_sync(kFull, base, 0);
+    if (base == kNone) return;
+    reinterpret_cast<uint2 *>(P.pool + base)[lane] =
+        make_uint2((h0 & 0xFFFFu) | (h1 << 16), (h2 & 0xFFFFu) | (h3 << 16));
 }
 
 // Single-search variant of one individual pattern on the staged stage, stored
