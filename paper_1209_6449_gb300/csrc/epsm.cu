@@ -23,6 +23,10 @@
 
 using namespace epsm;
 
+namespace {
+constexpr uint32_t kMaxRanges = 16384;  // range-total scratch of a context (emit ranges)
+}
+
 #define EPSM_API extern "C" __attribute__((visibility("default")))
 
 namespace {
@@ -184,8 +188,8 @@ epsm_status mark_done(epsm_ctx *c, cudaStream_t s) {
 // masks (256 B) per segment, i.e. n/512 + n/8 bytes; status words for the blocks.
 epsm_status ensure_stream_scratch(epsm_ctx *c, uint64_t nstages, cudaStream_t s) {
     if (!c->range_total) {
-        CK(cudaMalloc(&c->range_total, stream::kMaxBlocks * sizeof(unsigned long long)));
-        CK(cudaMemsetAsync(c->range_total, 0, stream::kMaxBlocks * sizeof(unsigned long long), s));
+        CK(cudaMalloc(&c->range_total, kMaxRanges * sizeof(unsigned long long)));
+        CK(cudaMemsetAsync(c->range_total, 0, kMaxRanges * sizeof(unsigned long long), s));
     }
     const uint64_t nseg = nstages * stream::kConsumerWarps;
     if (nseg <= c->seg_cap) return EPSM_OK;
@@ -203,11 +207,27 @@ epsm_status ensure_stream_scratch(epsm_ctx *c, uint64_t nstages, cudaStream_t s)
 }
 
 
-// Single searches run the cooperative streaming kernel (epsm_stream.cuh): one
-// block per SM, all co-resident.
+// Emit ranges of a single search: when positions are wanted, many (claimed
+// dynamically by the emission kernel), each at least one batch of 256
+// segments (32 stages); for a count only, one per filter block.
+
+int stream_emit_grid(int sms) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stream_emit_kernel, stream::kEmitThreads, 0) !=
+            cudaSuccess)
+            return 0;
+        per_sm = std::max(1, b);
+    }
+    return sms * per_sm;
+}
+
+// A single search: the streaming filter kernel (epsm_stream.cuh; up to two
+// blocks per SM), then, when positions are wanted, the emission kernel.
 template <int V, int MP>
 cudaError_t launch_stream_t(int sms, stream::StreamParams &p, cudaStream_t s) {
-    static int per_sm = 0;  // co-resident blocks per SM (cooperative launch bound)
+    static int per_sm = 0;
     const size_t smem = sizeof(stream::StreamSmem);
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(stream_kernel<V, MP>,
@@ -221,11 +241,19 @@ cudaError_t launch_stream_t(int sms, stream::StreamParams &p, cudaStream_t s) {
     }
     uint64_t grid = std::min<uint64_t>(std::max<uint64_t>(p.nstages, 1u), (uint64_t)sms * per_sm);
     grid = std::min<uint64_t>(grid, stream::kMaxBlocks);
-    // emit ranges of R stages; every block owns one range (possibly empty)
-    p.range_stages = std::max<uint64_t>(1, (p.nstages + grid - 1) / grid);
-    void *args[] = {(void *)&p};
-    return cudaLaunchCooperativeKernel((const void *)stream_kernel<V, MP>, dim3(grid),
-                                       dim3(stream::kThreadsStream), args, smem, s);
+    const uint64_t nst = std::max<uint64_t>(p.nstages, 1u);
+    const uint64_t want = p.emit ? std::max<uint64_t>(1, std::min<uint64_t>(nst / 32u, kMaxRanges))
+                                 : std::min<uint64_t>(grid, nst);
+    p.range_stages = (nst + want - 1) / want;
+    p.nranges = (uint32_t)((nst + p.range_stages - 1) / p.range_stages);
+    p.off = V == V_BLOCK8 ? -7 : 0;
+    stream_kernel<V, MP><<<(unsigned)grid, stream::kThreadsStream, smem, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !p.emit) return e;
+    const int eg = stream_emit_grid(sms);
+    if (eg == 0) return cudaErrorUnknown;
+    stream_emit_kernel<<<(unsigned)eg, stream::kEmitThreads, 0, s>>>(p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_stream(int sms, int v, uint32_t m, stream::StreamParams &p,
@@ -341,7 +369,7 @@ int emit_grid(int sms) {
     static int per_sm = 0;
     if (per_sm == 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, group_emit_kernel, group::kEmitThreads, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, group_emit_kernel, stream::kEmitThreads, 0) !=
             cudaSuccess)
             return 0;
         per_sm = std::max(1, b);
@@ -459,7 +487,7 @@ cudaError_t enqueue_batch(epsm_ctx *c, const group::Params &p, size_t up, size_t
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     group_kernel<<<R.grid, stream::kThreadsStream, sizeof(group::Smem), s>>>(p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    group_emit_kernel<<<R.egrid, group::kEmitThreads, 0, s>>>(p);
+    group_emit_kernel<<<R.egrid, stream::kEmitThreads, 0, s>>>(p);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return cudaMemcpyAsync(R.hoff, R.doff, down, cudaMemcpyDeviceToHost, s);
 }
@@ -515,7 +543,7 @@ void build_batch_graph(epsm_ctx *c) {
         void *args[] = {(void *)&p};
         kp.func = (void *)group_emit_kernel;
         kp.gridDim = dim3(R.egrid);
-        kp.blockDim = dim3(group::kEmitThreads);
+        kp.blockDim = dim3(stream::kEmitThreads);
         kp.kernelParams = args;
         e = cudaGraphAddKernelNode(&n_emit, g, &n_scan, 1, &kp);
     }
@@ -690,7 +718,7 @@ epsm_status batch_submit(epsm_ctx *c, uint32_t npairs, const uint8_t *const *tex
     // emit ranges, claimed dynamically by the emission kernel's blocks: many
     // (dense ranges take longer than sparse ones), each at least one batch of
     // 256 stages (one per emission thread), at most the range-total buffer
-    const uint64_t per_batch = (uint64_t)group::kEmitThreads;
+    const uint64_t per_batch = (uint64_t)stream::kEmitThreads;
     const uint64_t nr_want = std::max<uint64_t>(
         1, std::min<uint64_t>(jst / per_batch, (uint64_t)kRangesPerBlock * stream::kMaxBlocks));
     H.range_stages = (jst + nr_want - 1) / nr_want;
@@ -983,7 +1011,7 @@ constexpr uint64_t kStaticMaxStages =
 constexpr uint64_t kStaticMaxSegs = kStaticMaxStages * stream::kConsumerWarps;
 constexpr uint64_t kStaticCountBytes = kStaticMaxSegs * sizeof(uint32_t);
 constexpr uint64_t kStaticMaskBytes = kStaticMaxSegs * stream::kSegChunks * sizeof(uint16_t);
-constexpr uint64_t kStaticMiscBytes = 256 + stream::kMaxBlocks * 8;  // DevMisc + range totals
+constexpr uint64_t kStaticMiscBytes = 256 + kMaxRanges * 8;  // DevMisc + range totals
 constexpr uint64_t kStaticBytes = kStaticMiscBytes + kStaticCountBytes + kStaticMaskBytes;
 
 // In host code `g_static_scratch` only names the symbol; its device address

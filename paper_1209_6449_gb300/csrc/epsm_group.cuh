@@ -183,9 +183,8 @@ struct alignas(128) Smem {
     uint32_t pend[kConsumerWarps];               //   and its end
 };
 
-// Shared memory of the emission kernel (one block: 8 warps).
-constexpr int kEmitWarps = 8;
-constexpr int kEmitThreads = kEmitWarps * 32;
+// Shared memory of the emission kernel (one block: kEmitWarps = 8 warps, as
+// the single search's emission kernel).
 constexpr int kEmitSlices = kEmitThreads;  // the range totals are summed in this many slices
 struct alignas(16) EmitSmem {
     uint32_t spre[kEmitWarps][32 * 8];   // [lane * 8 + k]: hits before segment k of the lane's
@@ -1090,7 +1089,7 @@ __global__ void __launch_bounds__(stream::kThreadsStream, stream::kMaxBlocksPerS
 // block first takes the exclusive prefix of all range totals in 256 slices
 // (one per thread, one block scan) so that a claimed range's output offset is
 // its slice's prefix plus the totals before it in the slice.
-__global__ void __launch_bounds__(group::kEmitThreads, 4)
+__global__ void __launch_bounds__(stream::kEmitThreads, 4)
     group_emit_kernel(const __grid_constant__ group::Params P) {
     using namespace group;
     __shared__ EmitSmem S;

@@ -1,31 +1,30 @@
-// Streaming scan: filter pass, grid barrier, per-block prefix, emit pass —
-// in one cooperative persistent launch (up to two blocks per SM, all
-// co-resident).
+// Streaming scan of one search: a filter kernel and an emission kernel.
 //
 // The text is cut into 16 KiB stages (1024 chunks of 16 bytes) and each stage
 // into 8 segments of 128 chunks (2 KiB), one per consumer warp.
 //
-// Phase 1 (no ordering, no waiting on other blocks).  A producer warp claims
-// stages in batches from a global ticket (the next claim is requested while
-// the current batch is issued) and streams them through a ring of
-// shared-memory buffers with 1-D bulk copies (cp.async.bulk, completion on an
-// mbarrier), keeping up to kStages x 16 KiB of reads in flight per block.
-// Each consumer warp runs the variant's filter and verify (chunk_hits) on its
-// segment of each staged stage and writes the segment's hit count and, only if
-// it has hits, its 128 16-bit chunk masks to scratch.  Dynamic claiming keeps
-// every SM busy until the text is exhausted (a static split left the slowest
-// block ~40% behind the fastest).
-// Grid barrier (bounded).  All counts and masks are then written.
-// Phase 2.  Block b owns the emit range of stages [b*R, (b+1)*R).  The hit
-// total of every range was accumulated in phase 1; one warp sums the totals
-// of the ranges before the block's own (one round of loads).
-// Phase 3.  Consumer warps prefix-sum the segment counts of the range in order
-// and emit the positions of every segment with hits: the hit offsets are
-// staged in shared memory in output order, then written as consecutive 8-byte
-// positions (coalesced stores).
+// stream_kernel (persistent, two blocks per SM; no ordering, no waiting on
+// other blocks).  A producer warp claims stages in batches from a global
+// ticket (the next claim is requested while the current batch is issued) and
+// streams them through a ring of shared-memory buffers with 1-D bulk copies
+// (cp.async.bulk, completion on an mbarrier), keeping up to kStages x 16 KiB
+// of reads in flight per block.  Each consumer warp runs the variant's filter
+// and verify (chunk_hits) on its segment of each staged stage and writes the
+// segment's hit count, adds it to its emit range's total, and, only if it has
+// hits, writes its 128 16-bit chunk masks to scratch.  Dynamic claiming keeps
+// every SM busy until the text is exhausted.
+//
+// stream_emit_kernel (as many blocks as fit, launched after it when positions
+// are wanted).  Each block takes the exclusive prefix of the range totals
+// (256 slices, one block scan), then claims emit ranges dynamically: a batch
+// of 256 segment counts at a time, one block scan, and each warp expands its
+// segments with hits into positions (masks loaded ahead; hit offsets staged
+// in shared memory in output order, then written as consecutive 8-byte
+// positions).  Dense ranges take longer than sparse ones; dynamic claiming
+// balances them.
 //
 // Every wait is bounded in time; on expiry the error word gets kErrTimeout and
-// the waiting warp gives up, so the kernel always ends.  The producer waits,
+// the waiting warp gives up, so the kernels always end.  The producer waits,
 // again bounded, for its last bulk copies before the block can end.
 #pragma once
 
@@ -56,10 +55,6 @@ struct alignas(128) StreamSmem {
     uint64_t empty[kStages];
     uint32_t pblk[16];
     uint8_t table[kHashSlots];
-    uint16_t emit_stage[kConsumerWarps][32 * 16];  // per-warp staging of hit offsets
-    uint32_t scan_tmp[kConsumerWarps];
-    uint64_t cta_excl;
-    uint64_t cta_total;
 };
 
 // ---------------------------------------------------------------------------
@@ -141,7 +136,9 @@ struct StreamParams {
     uint32_t *err;
     DevMisc *misc;         // claim ticket, done counter, grid-barrier counter
     unsigned long long *range_total;  // scratch: hits per emit range (zero between calls)
-    uint64_t range_stages; // stages per emit range: block b emits [b*R, (b+1)*R)
+    uint64_t range_stages; // stages per emit range
+    uint32_t nranges;      // emit ranges (claimed dynamically by the emission kernel)
+    int32_t off;           // start of bit 0 of a chunk relative to it (-7: block variant)
     uint64_t nstages;      // 16 KiB stages of the text
     uint64_t chunk_full0;  // first chunk lying fully inside [delta, lim)
     uint64_t chunk_full1;  // one past the last such chunk
@@ -431,29 +428,43 @@ __device__ __forceinline__ void emit_list(uint32_t todo, uint64_t first, uint64_
 // in batches of 256 segments, and emission of the segments with hits.  Each
 // warp walks its segments with hits and loads the next one's masks before it
 // emits the current one, so mask loads overlap the stores.
-template <int OFF>
-__device__ __forceinline__ void emit_block(const StreamParams &P, StreamSmem &S, uint64_t st0,
-                                           uint64_t st1, int w, int lane) {
+// Shared memory of the emission kernel (one block: 8 warps).
+constexpr int kEmitWarps = 8;
+constexpr int kEmitThreads = kEmitWarps * 32;
+struct alignas(16) StreamEmitSmem {
+    uint16_t emit_stage[kEmitWarps][32 * 16];  // per-warp staging of hit offsets
+    uint32_t scan_tmp[kEmitWarps];
+    uint64_t scan64[kEmitWarps];
+    uint64_t slice_pre[kEmitThreads];          // exclusive prefix of the slices' range totals
+    uint64_t range_base;
+    uint32_t claim;
+};
+
+// Ordered emission of the stages [st0, st1) from output offset base0:
+// batches of 256 segments, a block scan of their counts, and each warp emits
+// its segments with hits (their masks loaded ahead, see emit_list).
+__device__ __forceinline__ void emit_stages(const StreamParams &P, StreamEmitSmem &S, uint64_t st0,
+                                            uint64_t st1, uint64_t base0, int w, int lane) {
     const int t = w * 32 + lane;
     const uint64_t seg0 = st0 * kConsumerWarps, seg1 = st1 * kConsumerWarps;
-    uint64_t base = S.cta_excl;
-    for (uint64_t sb = seg0; sb < seg1; sb += kConsumerWarps * 32) {
+    uint64_t base = base0;
+    const int64_t seg_pos0 = (int64_t)P.off - (int64_t)P.job.delta;
+    for (uint64_t sb = seg0; sb < seg1; sb += kEmitThreads) {
         const uint64_t seg = sb + (uint64_t)t;
         const uint32_t c = seg < seg1 ? P.seg_count[seg] : 0u;
         const uint32_t inc = warp_incl_scan(c, lane);
         if (lane == 31) S.scan_tmp[w] = inc;
-        consumer_sync();
+        __syncthreads();
         uint32_t wbase = 0u, btotal = 0u;
 #pragma unroll
-        for (int k = 0; k < kConsumerWarps; ++k) {
+        for (int k = 0; k < kEmitWarps; ++k) {
             const uint32_t v = S.scan_tmp[k];
             if (k < w) wbase += v;
             btotal += v;
         }
-        consumer_sync();
+        __syncthreads();
         const uint64_t excl = base + wbase + inc - c;
         const uint32_t todo = __ballot_sync(kFull, c != 0u);
-        const int64_t seg_pos0 = OFF - (int64_t)P.job.delta;
         emit_list(todo, sb + (uint64_t)w * 32u, excl, P.seg_mask, lane,
                   [&](uint64_t sj, uint64_t ej, uint2 packed) {
                       const int64_t s0 = (int64_t)(sj * kSegChunks * 16u) + seg_pos0;
@@ -464,37 +475,25 @@ __device__ __forceinline__ void emit_block(const StreamParams &P, StreamSmem &S,
     }
 }
 
-// The last block to finish resets the claim/barrier counters and zeroes the
-// range totals for the next launch (they are read by all blocks in phase 2,
-// which every block has passed by then).
+// The last block of the filter kernel resets the claim counters; when only
+// the count is wanted it also sums the range totals into count_out and
+// clears them (otherwise the emission kernel does both).
 __device__ __forceinline__ void finish_stream(const StreamParams &P) {
     __threadfence();
     const uint32_t d = atomicAdd(&P.misc->done, 1u);
     if (d == gridDim.x - 1u) {
-        for (uint32_t b = 0; b < gridDim.x; ++b) P.range_total[b] = 0ull;
+        if (!P.emit) {
+            uint64_t all = 0;
+            for (uint32_t r = 0; r < P.nranges; ++r) {
+                all += ld_relaxed_u64(reinterpret_cast<const uint64_t *>(P.range_total) + r);
+                P.range_total[r] = 0ull;
+            }
+            *P.count_out = all;
+        }
         P.misc->ticket = 0u;
         P.misc->done = 0u;
-        P.misc->barrier = 0u;
         __threadfence();
     }
-}
-
-// Grid-wide barrier of the co-resident blocks (called by one thread per
-// block, between __syncthreads): bounded wait on an arrival counter that the
-// last block to finish resets.
-__device__ __forceinline__ bool grid_barrier(DevMisc *misc) {
-    __threadfence();
-    atomicAdd(&misc->barrier, 1u);
-    const uint64_t t0 = globaltimer_ns();
-    for (;;) {
-        uint32_t v;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&misc->barrier) : "memory");
-        if (v >= gridDim.x) break;
-        if (globaltimer_ns() - t0 > kWaitNs) return false;
-        __nanosleep(128);
-    }
-    __threadfence();
-    return true;
 }
 
 }  // namespace stream
@@ -503,7 +502,6 @@ template <int V, int MP>
 __global__ void __launch_bounds__(stream::kThreadsStream, stream::kMaxBlocksPerSm)
     stream_kernel(const __grid_constant__ stream::StreamParams P) {
     using namespace stream;
-    constexpr int OFF = (V == V_BLOCK8) ? -7 : 0;
     extern __shared__ __align__(128) uint8_t smem_raw[];
     StreamSmem &S = *reinterpret_cast<StreamSmem *>(smem_raw);
     const int warp = threadIdx.x >> 5;
@@ -528,39 +526,78 @@ __global__ void __launch_bounds__(stream::kThreadsStream, stream::kMaxBlocksPerS
         if (!ok && lane == 0) atomicOr(P.err, kErrTimeout);
     }
     __syncthreads();
-    if (threadIdx.x == 0 && !grid_barrier(P.misc)) atomicOr(P.err, kErrTimeout);
-    __syncthreads();
+    if (threadIdx.x == 0) finish_stream(P);
+}
 
-    // phase 2: the totals of all emit ranges are final after the barrier; sum
-    // those before this block's range (one round of loads)
-    const uint64_t st0 = (uint64_t)blockIdx.x * P.range_stages;
-    const uint64_t st1 = st0 + P.range_stages < P.nstages ? st0 + P.range_stages : P.nstages;
-    if (warp == 0) {
+// Emission of a single search (after stream_kernel, when positions are
+// wanted): each block takes the exclusive prefix of the range totals in 256
+// slices, then claims ranges dynamically and emits them in order; block 0
+// writes the total, and the last block clears the range totals and the claim
+// counters for the next search.
+__global__ void __launch_bounds__(stream::kEmitThreads, 4)
+    stream_emit_kernel(const __grid_constant__ stream::StreamParams P) {
+    using namespace stream;
+    __shared__ StreamEmitSmem S;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const uint32_t nr = P.nranges;
+    const uint32_t per = (nr + kEmitThreads - 1) / kEmitThreads;
+    const uint64_t *rt = reinterpret_cast<const uint64_t *>(P.range_total);
+    {
+        const uint32_t r0 = (uint32_t)t * per, r1 = r0 + per < nr ? r0 + per : nr;
+        uint64_t sum = 0;
+#pragma unroll 8
+        for (uint32_t r = r0; r < r1; ++r) sum += rt[r];
+        uint64_t inc = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint64_t v = __shfl_up_sync(kFull, inc, d);
+            if (lane >= d) inc += v;
+        }
+        if (lane == 31) S.scan64[warp] = inc;
+        __syncthreads();
         uint64_t before = 0, all = 0;
-        for (uint32_t b = lane; b < gridDim.x; b += 32) {
-            const uint64_t v = ld_relaxed_u64(reinterpret_cast<const uint64_t *>(P.range_total) + b);
+#pragma unroll
+        for (int k = 0; k < kEmitWarps; ++k) {
+            const uint64_t v = S.scan64[k];
+            if (k < warp) before += v;
             all += v;
-            if (b < blockIdx.x) before += v;
         }
-        before = warp_sum64(before);
-        all = warp_sum64(all);
-        if (lane == 0) {
-            S.cta_excl = before;
-            S.cta_total = 0;
+        S.slice_pre[t] = before + inc - sum;
+        if (t == 0 && blockIdx.x == 0) *P.count_out = all;
+        __syncthreads();
+    }
+    for (;;) {
+        if (t == 0) S.claim = atomicAdd(&P.misc->ticket2, 1u);
+        __syncthreads();
+        const uint32_t r = S.claim;
+        if (r >= nr) break;
+        if (warp == 0) {
+            const uint32_t sl = r / per;
+            uint64_t part = 0;
+            for (uint32_t q = sl * per + (uint32_t)lane; q < r; q += 32) part += rt[q];
+            part = warp_sum64(part);
+            if (lane == 0) S.range_base = S.slice_pre[sl] + part;
         }
-        const uint64_t mine = ld_relaxed_u64(reinterpret_cast<const uint64_t *>(P.range_total) + blockIdx.x);
-        if (lane == 0) {
-            S.cta_total = mine;
-            if (blockIdx.x + 1 == gridDim.x) *P.count_out = all;
-        }
+        __syncthreads();
+        const uint64_t st0 = (uint64_t)r * P.range_stages;
+        const uint64_t st1 = st0 + P.range_stages < P.nstages ? st0 + P.range_stages : P.nstages;
+        if (st0 < st1 && rt[r] != 0ull) emit_stages(P, S, st0, st1, S.range_base, warp, lane);
+        __syncthreads();
+    }
+    // the last block to finish clears the range totals and the counters
+    if (t == 0) {
+        __threadfence();
+        S.claim = atomicAdd(&P.misc->done2, 1u) == gridDim.x - 1u ? 1u : 0u;
     }
     __syncthreads();
-
-    // phase 3: ordered emit
-    if (P.emit && warp < kConsumerWarps && S.cta_total != 0ull)
-        emit_block<OFF>(P, S, st0, st1, warp, lane);
-    __syncthreads();
-    if (threadIdx.x == 0) finish_stream(P);
+    if (S.claim) {
+        for (uint32_t r = (uint32_t)t; r < nr; r += kEmitThreads) P.range_total[r] = 0ull;
+        if (t == 0) {
+            P.misc->ticket2 = 0u;
+            P.misc->done2 = 0u;
+        }
+        __threadfence();
+    }
 }
 
 }  // namespace epsm
