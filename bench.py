@@ -472,10 +472,11 @@ def main():
     bytes_per_step = nsearch * TEXT_N
     value = world * bytes_per_step * args.steps / (elapsed_ms / 1e3) / 1e9
     occ_total = int(occ.sum())
-    # roofline of the scan kernel: algorithmic bytes = text read + 8 B per
-    # written position + 8 B count, per launch; duration = timed region / launches
+    # roofline of one search (the filter kernel and its emission kernel):
+    # algorithmic bytes = text read + 8 B per written position + 8 B count;
+    # duration = timed region / searches
     alg_bytes_per_launch = (bytes_per_step + 8 * occ_total + 8 * nsearch) / nsearch
-    per_launch_s = elapsed_ms / 1e3 / max(launches, 1)
+    per_launch_s = elapsed_ms / 1e3 / max(args.steps * nsearch, 1)
     achieved = alg_bytes_per_launch / per_launch_s / 1e9
     peak, peak_kind = measured_peaks()
     traffic = profiled_traffic()
@@ -505,7 +506,8 @@ def main():
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                              "unit": "GB/s", "frac": round(achieved / peak, 4),
                              "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                             "kernel": "scan_kernel (all variants; algorithmic bytes = n + 8*occ + 8 per launch)",
+                             "kernel": "stream_kernel + stream_emit_kernel, per search (all variants; "
+                                       "algorithmic bytes = n + 8*occ + 8 per search)",
                              "traffic": traffic.get("bytes_per_launch") if traffic else None,
                              "traffic_note": (traffic.get("note") if traffic else
                                               "null: no ncu capture of the current kernel sources")},

@@ -59,7 +59,10 @@ typedef enum {
     EPSM_VARIANT_DIRECT = 1,   /* packed window compare, 1 <= m <= 4   (Section 3.2, EPSMa) */
     EPSM_VARIANT_PREFIX4 = 2,  /* 4-byte first-bytes filter + verify, 4 <= m <= 15 (Section 3.3, EPSMb) */
     EPSM_VARIANT_PREFIX8 = 3,  /* 8-byte first-bytes filter + verify, 8 <= m <= 15 (Section 3.3, EPSMb with m' = 8) */
-    EPSM_VARIANT_BLOCK8 = 4    /* aligned 8-byte block fingerprint + verify, 15 <= m <= 32 (Section 3.4, EPSMc) */
+    EPSM_VARIANT_BLOCK8 = 4,   /* aligned 8-byte block fingerprint + verify, 15 <= m <= 32 (Section 3.4, EPSMc) */
+    EPSM_VARIANT_BLOCK4 = 5    /* aligned 4-byte blocks compared with the pattern's 4 blocks + verify,
+                                  7 <= m <= 16 (Section 3.4's aligned-block idea with 4-byte blocks;
+                                  segments where blocks match often use the Section 3.3 prefix filter) */
 } epsm_variant;
 
 /* Create a context on CUDA device `device`.  `flags` is reserved (pass 0).

@@ -33,8 +33,8 @@ namespace {
 
 int default_variant(uint32_t m) {
     if (m <= 4) return V_DIRECT;
-    if (m <= 7) return V_PREFIX4;
-    if (m <= 14) return V_PREFIX8;
+    if (m <= 6) return V_PREFIX4;
+    if (m <= 14) return V_BLOCK4;
     return V_BLOCK8;
 }
 
@@ -44,6 +44,7 @@ bool variant_covers(int v, uint32_t m) {
         case V_PREFIX4: return m >= 4 && m <= 15;
         case V_PREFIX8: return m >= 8 && m <= 15;
         case V_BLOCK8: return m >= 15 && m <= 32;
+        case V_BLOCK4: return m >= 7 && m <= 16;
         default: return false;
     }
 }
@@ -246,7 +247,7 @@ cudaError_t launch_stream_t(int sms, stream::StreamParams &p, cudaStream_t s) {
                                  : std::min<uint64_t>(grid, nst);
     p.range_stages = (nst + want - 1) / want;
     p.nranges = (uint32_t)((nst + p.range_stages - 1) / p.range_stages);
-    p.off = V == V_BLOCK8 ? -7 : 0;
+    p.off = variant_offset(V);
     stream_kernel<V, MP><<<(unsigned)grid, stream::kThreadsStream, smem, s>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !p.emit) return e;
@@ -268,6 +269,7 @@ cudaError_t launch_stream(int sms, int v, uint32_t m, stream::StreamParams &p,
             }
         case V_PREFIX4: return launch_stream_t<V_PREFIX4, 4>(sms, p, s);
         case V_PREFIX8: return launch_stream_t<V_PREFIX8, 8>(sms, p, s);
+        case V_BLOCK4: return launch_stream_t<V_BLOCK4, 4>(sms, p, s);
         default: return launch_stream_t<V_BLOCK8, 8>(sms, p, s);
     }
 }
@@ -314,7 +316,7 @@ epsm_status search_async_impl(epsm_ctx *c, int variant, const uint8_t *text, uin
     p.err = &c->misc->err;
     p.misc = c->misc;
     CK(launch_stream(c->sms, v, m, p, s));
-    c->launches += 1;
+    c->launches += p.emit ? 2 : 1;  // filter kernel (+ emission kernel)
     return mark_done(c, s);
 }
 
@@ -757,7 +759,7 @@ epsm_status batch_submit(epsm_ctx *c, uint32_t npairs, const uint8_t *const *tex
         }
     }
     if (!launched) CK(enqueue_batch(c, batch_params(c), up, down, s));
-    c->launches += 2;  // table build + batched scan
+    c->launches += 3;  // table build + batched filter + emission
     CK(cudaMemcpyAsync(c->hmisc, c->misc, sizeof(DevMisc), cudaMemcpyDeviceToHost, s));
     return mark_done(c, s);
 }

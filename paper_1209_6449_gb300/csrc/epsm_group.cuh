@@ -475,10 +475,12 @@ __device__ __noinline__ void plain_job(const Params &P, const Header &H, Smem &S
     const uint32_t *pb = tb ? reinterpret_cast<const uint32_t *>(tb + kHashSlots) : nullptr;
     const uint64_t cf0 = (D.job.delta + 15u) / 16u, cf1 = D.job.lim / 16u;
     uint32_t h[4] = {0u, 0u, 0u, 0u};
+    bool dense = false;  // the 4-byte block variant probes every segment here
     switch (D.variant) {  // (store_list counts the hits from the masks)
         case V_DIRECT: stage_hits<V_DIRECT, 0>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
         case V_PREFIX4: stage_hits<V_PREFIX4, 4>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
         case V_PREFIX8: stage_hits<V_PREFIX8, 8>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
+        case V_BLOCK4: stage_hits<V_BLOCK4, 4, true>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h, &dense); break;
         default: stage_hits<V_BLOCK8, 8>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
     }
     const uint64_t st = D.stage0 + ls;

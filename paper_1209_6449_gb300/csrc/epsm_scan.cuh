@@ -28,6 +28,7 @@ constexpr int V_DIRECT = 1;
 constexpr int V_PREFIX4 = 2;
 constexpr int V_PREFIX8 = 3;
 constexpr int V_BLOCK8 = 4;
+constexpr int V_BLOCK4 = 5;
 
 // Block fingerprint table (Section 3.4): k = 11 bits -> 2048 one-byte slots.
 constexpr int kHashBits = 11;
@@ -175,6 +176,35 @@ __device__ __noinline__ bool verify_global(const SearchJob &J, int64_t P) {
         cur = nxt;
     }
     return true;
+}
+
+// Where a candidate can be checked from: the staged stage buffer holds the
+// text's internal bytes [sbase, sbase + span) when `inside` is set.
+struct StagedText {
+    const uint8_t *buf;
+    int64_t sbase;
+    uint32_t span;
+    uint32_t inside;
+};
+
+// t[P..P+m) == p, read from the staged bytes when they cover it (shared
+// memory word loads), else from global memory.
+__device__ __forceinline__ bool verify_staged(const SearchJob &J, int64_t P, const StagedText &T) {
+    const int64_t o = P - T.sbase;
+    const uint32_t m = J.pat.m;
+    if (T.inside && o >= 0 && o + (int64_t)m <= (int64_t)T.span) {
+        const uint32_t *W = reinterpret_cast<const uint32_t *>(T.buf);
+        const uint32_t a = (uint32_t)o >> 2, sh = ((uint32_t)o & 3u) * 8u;
+        const uint32_t nw = (m + 3u) >> 2;
+        uint32_t cur = W[a];
+        for (uint32_t i = 0; i < nw; ++i) {
+            const uint32_t nxt = W[a + i + 1u];
+            if ((__funnelshift_r(cur, nxt, sh) ^ J.pat.w[i]) & word_mask(m, i)) return false;
+            cur = nxt;
+        }
+        return true;
+    }
+    return verify_global(J, P);
 }
 
 // ---------------------------------------------------------------------------

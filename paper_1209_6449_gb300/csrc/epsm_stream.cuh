@@ -46,6 +46,8 @@ constexpr int kMaxBlocksPerSm = 2;
 constexpr uint64_t kMaxBlocks = 512;                        // grid bound (range totals, status words)
 
 constexpr uint32_t kClaim = 2;                              // stages per claim
+constexpr int kBlock4Dense = 2;   // steps of 4 with a block match somewhere: use the prefix filter
+constexpr int kBlock4Epoch = 32;  // segments a warp filters with the prefix filter before it re-probes
 constexpr uint64_t kEndStage = ~0ull;
 
 struct alignas(128) StreamSmem {
@@ -244,24 +246,59 @@ __device__ __forceinline__ void load_segment(const SearchJob &J, uint64_t cf0, u
 // the stage holds the job's chunks c0 .. c0+1024 (+ halo); lane l takes chunks
 // 32u + l of segment w.  Writes the four 16-bit hit masks to h and returns the
 // lane's hit count.
-template <int V, int MP>
+//   PROBE (4-byte block variant only): first decide from the segment whether
+//   the text is dense in block matches (`dense`), and if so filter it with
+//   the prefix filter instead.
+template <int V, int MP, bool PROBE = false>
 __device__ __forceinline__ uint32_t stage_hits(const SearchJob &J, uint64_t cf0, uint64_t cf1,
                                                const BcastWords &B, const uint8_t *table,
                                                const uint32_t *pblk, const uint8_t *buf,
-                                               uint64_t c0, int w, int lane, uint32_t (&h)[4]) {
+                                               uint64_t c0, int w, int lane, uint32_t (&h)[4],
+                                               bool *dense_out = nullptr) {
     constexpr int OFF = (V == V_BLOCK8) ? -7 : 0;
     uint4 ch[4];
     uint4 halo;
     load_segment(J, cf0, cf1, buf, c0, w, lane, V != V_BLOCK8, ch, halo);
+    StagedText T;
+    T.buf = buf;
+    T.sbase = (int64_t)(c0 * 16u);
+    T.span = (uint32_t)((kStageChunks + 1) * 16);
+    T.inside = (c0 >= cf0 && c0 + kStageChunks + 1u <= cf1) ? 1u : 0u;
     const int64_t sp0 = (int64_t)((c0 + (uint64_t)w * kSegChunks) * 16u) + OFF;
     const bool interior = sp0 >= (int64_t)J.delta && sp0 + (int64_t)(kSegChunks * 16) - 1 <= J.pmax;
+    // 4-byte block variant: a probe of the segment decides whether the text
+    // makes block matches frequent (small alphabets: most steps would take
+    // the candidate path); then the prefix filter of Section 3.3 is cheaper,
+    // with the same start offset and masks.
+    bool dense = false;
+    if constexpr (V == V_BLOCK4 && PROBE) {
+        {
+            uint32_t q0, q1, q2, q3;
+            pattern_blocks4(J.pat, q0, q1, q2, q3);
+            int steps = 0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint4 ns = (lane == 0) ? (u + 1 < 4 ? ch[u + 1 < 4 ? u + 1 : u] : halo) : ch[u];
+                const uint32_t n0 = __shfl_sync(kFull, ns.x, (lane + 1) & 31);
+                steps += __any_sync(kFull, block4_any(ch[u], n0, q0, q1, q2, q3)) ? 1 : 0;
+            }
+            dense = steps >= kBlock4Dense;
+        }
+        *dense_out = dense;
+    }
     uint32_t cnt = 0u;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const uint4 cur = ch[u];
         const uint4 nsrc = (lane == 0) ? (u + 1 < 4 ? ch[u + 1 < 4 ? u + 1 : u] : halo) : cur;
         const int64_t p0 = sp0 + (int64_t)((32 * u + lane) * 16);
-        uint32_t hh = chunk_hits<V, MP>(J, cur, nsrc, p0, B, table, pblk, lane);
+        uint32_t hh;
+        if (V == V_BLOCK4 && PROBE && dense) {
+            hh = J.pat.m >= 8u ? chunk_hits<V_PREFIX8, 8>(J, cur, nsrc, p0, B, table, pblk, lane, T)
+                               : chunk_hits<V_PREFIX4, 4>(J, cur, nsrc, p0, B, table, pblk, lane, T);
+        } else {
+            hh = chunk_hits<V, MP>(J, cur, nsrc, p0, B, table, pblk, lane, T);
+        }
         if (!interior) hh &= range_mask((int64_t)J.delta - p0, J.pmax - p0);
         h[u] = hh;
         cnt += __popc(hh);
@@ -275,13 +312,17 @@ __device__ __forceinline__ void store_segment(uint32_t *seg_count, uint16_t *seg
                                               unsigned long long *range_total,
                                               uint64_t range_stages, uint64_t st, uint64_t seg,
                                               uint32_t cnt, const uint32_t (&h)[4], bool emit,
-                                              int lane) {
+                                              int lane, uint64_t &acc) {
     const uint32_t wc = __any_sync(kFull, cnt != 0u) ? warp_sum(cnt) : 0u;
+    if (!emit) {  // count only: the warp adds its total once, at the end
+        acc += wc;
+        return;
+    }
     if (lane == 0) {
         seg_count[seg] = wc;
         if (wc) atomicAdd(&range_total[st / range_stages], (unsigned long long)wc);
     }
-    if (wc != 0u && emit) {
+    if (wc != 0u) {
         uint2 packed;
         packed.x = (h[0] & 0xFFFFu) | (h[1] << 16);
         packed.y = (h[2] & 0xFFFFu) | (h[3] << 16);
@@ -289,27 +330,63 @@ __device__ __forceinline__ void store_segment(uint32_t *seg_count, uint16_t *seg
     }
 }
 
+// One segment of the warp's ring: wait for the next stage, filter the warp's
+// segment of it, release the buffer and store the results.  Returns false at
+// the end of the stream (or when a wait gave up, with *ok cleared).
+template <int V, int MP, bool PROBE>
+__device__ __forceinline__ bool one_segment(const StreamParams &P, StreamSmem &S, const BcastWords &B,
+                                            int &s, uint32_t &phase, int w, int lane, bool *ok,
+                                            uint64_t &acc, bool *dense) {
+    if (!warp_wait(&S.full[s], phase)) { *ok = false; return false; }
+    const uint64_t st = S.stage_id[s];
+    if (st == kEndStage) return false;
+    uint32_t h[4];
+    const uint32_t cnt = stage_hits<V, MP, PROBE>(P.job, P.chunk_full0, P.chunk_full1, B, S.table,
+                                                  S.pblk, S.buf[s], st * kStageChunks, w, lane, h,
+                                                  dense);
+    // the stage buffer is no longer needed: release it to the producer
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.empty[s]);
+    if (++s == kStages) { s = 0; phase ^= 1u; }
+    store_segment(P.seg_count, P.seg_mask, P.range_total, P.range_stages, st,
+                  st * kConsumerWarps + (uint64_t)w, cnt, h, P.emit != 0, lane, acc);
+    return true;
+}
+
 template <int V, int MP>
 __device__ __forceinline__ void filter_stages(const StreamParams &P, StreamSmem &S, int w, int lane,
                                               bool *ok) {
-    const SearchJob &J = P.job;
-    const BcastWords B(J.pat);
+    const BcastWords B(P.job.pat);
     int s = 0;
     uint32_t phase = 0;
-    for (;;) {
-        if (!warp_wait(&S.full[s], phase)) { *ok = false; break; }
-        const uint64_t st = S.stage_id[s];
-        if (st == kEndStage) break;
-        uint32_t h[4];
-        const uint32_t cnt = stage_hits<V, MP>(J, P.chunk_full0, P.chunk_full1, B, S.table, S.pblk,
-                                               S.buf[s], st * kStageChunks, w, lane, h);
-        // the stage buffer is no longer needed: release it to the producer
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&S.empty[s]);
-        if (++s == kStages) { s = 0; phase ^= 1u; }
-        store_segment(P.seg_count, P.seg_mask, P.range_total, P.range_stages, st,
-                      st * kConsumerWarps + (uint64_t)w, cnt, h, P.emit != 0, lane);
+    uint64_t acc = 0;
+    if constexpr (V == V_BLOCK4) {
+        // Epochs: one probing segment decides the mode, then the warp runs
+        // that mode's own loop (no per-segment branch between the filters)
+        // until it probes again -- at once while the text stays sparse in
+        // block matches, after kBlock4Epoch segments of the prefix filter.
+        const bool p8 = P.job.pat.m >= 8u;
+        bool more = true;
+        while (more) {
+            bool dense = false;
+            more = one_segment<V_BLOCK4, 4, true>(P, S, B, s, phase, w, lane, ok, acc, &dense);
+            if (!more) break;
+            if (!dense) {
+                for (int k = 0; more && k < kBlock4Epoch; ++k)
+                    more = one_segment<V_BLOCK4, 4, false>(P, S, B, s, phase, w, lane, ok, acc, nullptr);
+            } else if (p8) {
+                for (int k = 0; more && k < kBlock4Epoch; ++k)
+                    more = one_segment<V_PREFIX8, 8, false>(P, S, B, s, phase, w, lane, ok, acc, nullptr);
+            } else {
+                for (int k = 0; more && k < kBlock4Epoch; ++k)
+                    more = one_segment<V_PREFIX4, 4, false>(P, S, B, s, phase, w, lane, ok, acc, nullptr);
+            }
+        }
+    } else {
+        while (one_segment<V, MP, false>(P, S, B, s, phase, w, lane, ok, acc, nullptr)) {
+        }
     }
+    if (!P.emit && lane == 0 && acc) atomicAdd(&P.range_total[blockIdx.x % P.nranges], (unsigned long long)acc);
 }
 
 // Emit the positions of one segment (a whole warp), given lane l's packed

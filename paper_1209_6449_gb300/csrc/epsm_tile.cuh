@@ -3,9 +3,11 @@
 // A chunk is 16 text bytes held as four little-endian 32-bit words; a lane
 // also sees the next chunk (its neighbour lane's, by a shuffle).  For each
 // chunk a 16-bit mask marks hits: bit i <-> internal start pos0 + OFF + i,
-// with pos0 = 16*chunk.  OFF = 0 for the window variants; the block variant
-// reports candidate s = 8b - j from block b, j in [0, 8), so a chunk's two
-// blocks cover starts [pos0 - 7, pos0 + 8] and OFF = -7.
+// with pos0 = 16*chunk.  OFF = 0 for the window variants; the 8-byte block
+// variant reports candidate s = 8b - j from block b, j in [0, 8), so a
+// chunk's two blocks cover starts [pos0 - 7, pos0 + 8] and OFF = -7.  The
+// 4-byte block variant looks at the chunk's words and the next chunk's first
+// one (k = 0..4) and reports s = 4k - j for s in [pos0, pos0 + 15]: OFF = 0.
 #pragma once
 
 #include "epsm_scan.cuh"
@@ -97,7 +99,8 @@ __device__ __forceinline__ uint32_t verify_word_hits(uint32_t z, const uint32_t 
 // fingerprint slot.  Compare the blocks with the pattern blocks p[j..j+7]; a
 // block match at j gives the candidate 8b - j, which is checked in full.
 __device__ __noinline__ uint32_t block_candidates(const SearchJob &J, const uint4 cur, int64_t p0,
-                                                  const uint32_t *pblk, uint32_t t0, uint32_t t1) {
+                                                  const uint32_t *pblk, uint32_t t0, uint32_t t1,
+                                                  const StagedText &T) {
     uint32_t cand = 0u;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -110,9 +113,76 @@ __device__ __noinline__ uint32_t block_candidates(const SearchJob &J, const uint
         int i = __ffs(cand) - 1;
         cand &= cand - 1u;
         int64_t P = p0 + i;
-        if (P >= (int64_t)J.delta && P <= J.pmax && verify_global(J, P)) h |= 1u << i;
+        if (P >= (int64_t)J.delta && P <= J.pmax && verify_staged(J, P, T)) h |= 1u << i;
     }
     return h;
+}
+
+// Full in-register check of the start at byte 4K + b of the chunk (RR: the
+// chunk's words and the next chunk's; m <= 16).
+template <int K>
+__device__ __forceinline__ bool verify_all_regs(const uint32_t (&RR)[8], uint32_t b, const Pattern &pat) {
+    const uint32_t m = pat.m;
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if ((uint32_t)(4 * i) < m) {
+            const uint32_t win = __funnelshift_r(RR[K + i], RR[K + i + 1], 8u * b);
+            ok &= ((win ^ pat.w[i]) & word_mask(m, (uint32_t)i)) == 0u;
+        }
+    }
+    return ok;
+}
+
+// 4-byte block variant, slow path: a word k of the chunk (k = 0..3) or the
+// next chunk's first word (k = 4) equals a pattern block p[j..j+3] (q[j]); the
+// match gives the candidate start 4k - j when it lies in the chunk
+// (0 <= 4k - j <= 15), which is then checked in full in registers.
+__device__ __noinline__ uint32_t block4_candidates(const Pattern &pat, const uint4 cur, uint32_t n0,
+                                                   uint32_t n1, uint32_t n2, uint32_t n3,
+                                                   uint32_t q0, uint32_t q1, uint32_t q2, uint32_t q3) {
+    const uint32_t R[5] = {cur.x, cur.y, cur.z, cur.w, n0};
+    const uint32_t q[4] = {q0, q1, q2, q3};
+    uint32_t cand = 0u;
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (4 * k - j >= 0 && 4 * k - j <= 15 && R[k] == q[j]) cand |= 1u << (4 * k - j);
+    const uint32_t RR[8] = {cur.x, cur.y, cur.z, cur.w, n0, n1, n2, n3};
+    uint32_t h = 0u;
+    while (cand) {
+        const uint32_t i = (uint32_t)(__ffs(cand) - 1);
+        cand &= cand - 1u;
+        bool ok;
+        switch (i >> 2) {
+            case 0: ok = verify_all_regs<0>(RR, i & 3u, pat); break;
+            case 1: ok = verify_all_regs<1>(RR, i & 3u, pat); break;
+            case 2: ok = verify_all_regs<2>(RR, i & 3u, pat); break;
+            default: ok = verify_all_regs<3>(RR, i & 3u, pat); break;
+        }
+        if (ok) h |= 1u << i;
+    }
+    return h;
+}
+
+// The four pattern blocks p[j..j+3], j = 0..3, of the 4-byte block variant.
+__device__ __forceinline__ void pattern_blocks4(const Pattern &pat, uint32_t &q0, uint32_t &q1,
+                                                uint32_t &q2, uint32_t &q3) {
+    q0 = pat.w[0];
+    q1 = __funnelshift_r(pat.w[0], pat.w[1], 8);
+    q2 = __funnelshift_r(pat.w[0], pat.w[1], 16);
+    q3 = __funnelshift_r(pat.w[0], pat.w[1], 24);
+}
+
+// Block test of the 4-byte block variant: does some word of the chunk (or the
+// next chunk's first word) equal a pattern block at an offset that gives a
+// start inside the chunk?
+__device__ __forceinline__ bool block4_any(const uint4 cur, uint32_t n0, uint32_t q0, uint32_t q1,
+                                           uint32_t q2, uint32_t q3) {
+    return (cur.x == q0) | (cur.y == q0) | (cur.y == q1) | (cur.y == q2) | (cur.y == q3) |
+           (cur.z == q0) | (cur.z == q1) | (cur.z == q2) | (cur.z == q3) | (cur.w == q0) |
+           (cur.w == q1) | (cur.w == q2) | (cur.w == q3) | (n0 == q1) | (n0 == q2) | (n0 == q3);
 }
 
 // Hit mask of one chunk (before start-validity masking).
@@ -122,7 +192,8 @@ template <int V, int MP>
 __device__ __forceinline__ uint32_t chunk_hits(const SearchJob &J, const uint4 cur,
                                                const uint4 nsrc, int64_t p0,
                                                const BcastWords &B, const uint8_t *table,
-                                               const uint32_t *pblk, int lane) {
+                                               const uint32_t *pblk, int lane,
+                                               const StagedText &T) {
     const int src = (lane + 1) & 31;
     const Pattern &pat = J.pat;
     if constexpr (V == V_DIRECT) {
@@ -132,10 +203,10 @@ __device__ __forceinline__ uint32_t chunk_hits(const SearchJob &J, const uint4 c
         // compares of bytes at or past m are masked off.
         uint32_t n0 = __shfl_sync(kFull, nsrc.x, src);
         uint32_t R[5] = {cur.x, cur.y, cur.z, cur.w, n0};
-        uint32_t h = 0u;
         const uint32_t mk1 = (MP == 0 && pat.m <= 1u) ? 0u : 0xFFFFFFFFu;
         const uint32_t mk2 = (MP == 0 && pat.m <= 2u) ? 0u : 0xFFFFFFFFu;
         const uint32_t mk3 = (MP == 0 && pat.m <= 3u) ? 0u : 0xFFFFFFFFu;
+        uint32_t z[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             uint32_t X;
@@ -146,8 +217,13 @@ __device__ __forceinline__ uint32_t chunk_hits(const SearchJob &J, const uint4 c
             } else {
                 X = window_mismatch<MP>(0u, R[k], R[k + 1], B.b[0], B.b[1], B.b[2], B.b[3]);
             }
-            h |= nibble_of(zero_bytes(X)) << (4 * k);
+            z[k] = zero_bytes(X);
         }
+        // most chunks of a large alphabet have no match: skip the packing
+        if ((z[0] | z[1] | z[2] | z[3]) == 0u) return 0u;
+        uint32_t h = 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) h |= nibble_of(z[k]) << (4 * k);
         return h;
     } else if constexpr (V == V_PREFIX4) {
         // Section 3.3 (EPSMb) with a 4-byte prefix: exact prefix test per start,
@@ -203,6 +279,24 @@ __device__ __forceinline__ uint32_t chunk_hits(const SearchJob &J, const uint4 c
             }
         }
         return h;
+    } else if constexpr (V == V_BLOCK4) {
+        // Section 3.4's aligned-block idea with 4-byte blocks (7 <= m <= 16):
+        // every occurrence at s covers the aligned word at the first multiple
+        // of 4 in [s, s+3], equal to the pattern block p[j..j+3] with j that
+        // word's offset from s -- only four blocks, so each word is compared
+        // with all of them instead of hashing.
+        const uint32_t n0 = __shfl_sync(kFull, nsrc.x, src);
+        uint32_t q0, q1, q2, q3;
+        pattern_blocks4(pat, q0, q1, q2, q3);
+        const bool any = block4_any(cur, n0, q0, q1, q2, q3);
+        uint32_t h = 0u;
+        if (__any_sync(kFull, any)) {
+            const uint32_t n1 = __shfl_sync(kFull, nsrc.y, src);
+            const uint32_t n2 = __shfl_sync(kFull, nsrc.z, src);
+            const uint32_t n3 = __shfl_sync(kFull, nsrc.w, src);
+            if (any) h = block4_candidates(pat, cur, n0, n1, n2, n3, q0, q1, q2, q3);
+        }
+        return h;
     } else {
         // Section 3.4 (EPSMc) on aligned 8-byte blocks: fingerprint each block,
         // and where the slot is marked compare the block with the pattern
@@ -212,7 +306,7 @@ __device__ __forceinline__ uint32_t chunk_hits(const SearchJob &J, const uint4 c
         const uint32_t h1 = block_hash(cur.z, cur.w);
         const uint32_t t0 = table[h0];
         const uint32_t t1 = table[h1];
-        if (t0 | t1) return block_candidates(J, cur, p0, pblk, t0, t1);
+        if (t0 | t1) return block_candidates(J, cur, p0, pblk, t0, t1, T);
         return 0u;
     }
 }

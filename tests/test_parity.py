@@ -36,6 +36,7 @@ VARIANTS = {  # variant -> covered m
     2: range(4, 16),
     3: range(8, 16),
     4: range(15, 33),
+    5: range(7, 17),
 }
 
 
