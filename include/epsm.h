@@ -60,9 +60,13 @@ typedef enum {
     EPSM_VARIANT_PREFIX4 = 2,  /* 4-byte first-bytes filter + verify, 4 <= m <= 15 (Section 3.3, EPSMb) */
     EPSM_VARIANT_PREFIX8 = 3,  /* 8-byte first-bytes filter + verify, 8 <= m <= 15 (Section 3.3, EPSMb with m' = 8) */
     EPSM_VARIANT_BLOCK8 = 4,   /* aligned 8-byte block fingerprint + verify, 15 <= m <= 32 (Section 3.4, EPSMc) */
-    EPSM_VARIANT_BLOCK4 = 5    /* aligned 4-byte blocks compared with the pattern's 4 blocks + verify,
-                                  7 <= m <= 16 (Section 3.4's aligned-block idea with 4-byte blocks;
-                                  segments where blocks match often use the Section 3.3 prefix filter) */
+    EPSM_VARIANT_BLOCK4 = 5,   /* aligned 4-byte blocks compared with the pattern's 4 blocks + verify,
+                                  7 <= m <= 16 (Section 3.4's aligned-block idea with 4-byte blocks) */
+    EPSM_VARIANT_CODE2 = 6,    /* 2-bit codes (bits 1..2 of every byte) of the first min(m, 8) bytes
+                                  as the filter + verify, 2 <= m <= 16 (Section 3.3's filter-then-verify) */
+    EPSM_VARIANT_ADAPT = 7     /* 5 <= m <= 16: per warp and epoch of segments, the 2-bit code filter
+                                  where the text makes 4-byte block matches frequent (small alphabets),
+                                  else BLOCK4 (m >= 7) or PREFIX4 */
 } epsm_variant;
 
 /* Create a context on CUDA device `device`.  `flags` is reserved (pass 0).

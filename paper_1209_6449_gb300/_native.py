@@ -14,8 +14,9 @@ _lib = None
 OK, ERR_ARG, ERR_CAPACITY, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT = range(6)
 STATUS_NAMES = ["EPSM_OK", "EPSM_ERR_ARG", "EPSM_ERR_CAPACITY", "EPSM_ERR_CUDA",
                 "EPSM_ERR_NOMEM", "EPSM_ERR_TIMEOUT"]
-VARIANT_AUTO, VARIANT_DIRECT, VARIANT_PREFIX4, VARIANT_PREFIX8, VARIANT_BLOCK8, VARIANT_BLOCK4 = range(6)
-VARIANT_NAMES = {1: "direct", 2: "prefix4", 3: "prefix8", 4: "block8", 5: "block4"}
+(VARIANT_AUTO, VARIANT_DIRECT, VARIANT_PREFIX4, VARIANT_PREFIX8, VARIANT_BLOCK8, VARIANT_BLOCK4, VARIANT_CODE2,
+ VARIANT_ADAPT) = range(8)
+VARIANT_NAMES = {1: "direct", 2: "prefix4", 3: "prefix8", 4: "block8", 5: "block4", 6: "code2", 7: "adapt"}
 MAX_M = 32
 
 EXPORTS = ["epsm_create", "epsm_destroy", "epsm_status_str", "epsm_last_error",

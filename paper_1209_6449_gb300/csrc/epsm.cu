@@ -33,8 +33,7 @@ namespace {
 
 int default_variant(uint32_t m) {
     if (m <= 4) return V_DIRECT;
-    if (m <= 6) return V_PREFIX4;
-    if (m <= 14) return V_BLOCK4;
+    if (m <= 14) return V_ADAPT;
     return V_BLOCK8;
 }
 
@@ -45,6 +44,8 @@ bool variant_covers(int v, uint32_t m) {
         case V_PREFIX8: return m >= 8 && m <= 15;
         case V_BLOCK8: return m >= 15 && m <= 32;
         case V_BLOCK4: return m >= 7 && m <= 16;
+        case V_CODE2: return m >= 2 && m <= 16;
+        case V_ADAPT: return m >= 5 && m <= 16;
         default: return false;
     }
 }
@@ -210,7 +211,7 @@ epsm_status ensure_stream_scratch(epsm_ctx *c, uint64_t nstages, cudaStream_t s)
 
 // Emit ranges of a single search: when positions are wanted, many (claimed
 // dynamically by the emission kernel), each at least one batch of 256
-// segments (32 stages); for a count only, one per filter block.
+// segments (32 stages); for a count only, a single one.
 
 int stream_emit_grid(int sms) {
     static int per_sm = 0;
@@ -243,8 +244,8 @@ cudaError_t launch_stream_t(int sms, stream::StreamParams &p, cudaStream_t s) {
     uint64_t grid = std::min<uint64_t>(std::max<uint64_t>(p.nstages, 1u), (uint64_t)sms * per_sm);
     grid = std::min<uint64_t>(grid, stream::kMaxBlocks);
     const uint64_t nst = std::max<uint64_t>(p.nstages, 1u);
-    const uint64_t want = p.emit ? std::max<uint64_t>(1, std::min<uint64_t>(nst / 32u, kMaxRanges))
-                                 : std::min<uint64_t>(grid, nst);
+    // count only: one range, which every filter warp adds its total to once
+    const uint64_t want = p.emit ? std::max<uint64_t>(1, std::min<uint64_t>(nst / 32u, kMaxRanges)) : 1u;
     p.range_stages = (nst + want - 1) / want;
     p.nranges = (uint32_t)((nst + p.range_stages - 1) / p.range_stages);
     p.off = variant_offset(V);
@@ -270,6 +271,8 @@ cudaError_t launch_stream(int sms, int v, uint32_t m, stream::StreamParams &p,
         case V_PREFIX4: return launch_stream_t<V_PREFIX4, 4>(sms, p, s);
         case V_PREFIX8: return launch_stream_t<V_PREFIX8, 8>(sms, p, s);
         case V_BLOCK4: return launch_stream_t<V_BLOCK4, 4>(sms, p, s);
+        case V_CODE2: return launch_stream_t<V_CODE2, 4>(sms, p, s);
+        case V_ADAPT: return launch_stream_t<V_ADAPT, 4>(sms, p, s);
         default: return launch_stream_t<V_BLOCK8, 8>(sms, p, s);
     }
 }

@@ -461,8 +461,12 @@ __device__ __forceinline__ void store_list(const Params &P, const Header &H, Sme
     if (!H.emit) return;
     base = __shfl_sync(kFull, base, 0);
     if (base == kNone) return;
-    reinterpret_cast<uint2 *>(P.pool + base)[lane] =
-        make_uint2((h0 & 0xFFFFu) | (h1 << 16), (h2 & 0xFFFFu) | (h3 << 16));
+    // the 128 chunk masks in chunk order (lane l holds chunks 32u + l)
+    uint16_t *m = P.pool + base;
+    m[lane] = (uint16_t)h0;
+    m[32 + lane] = (uint16_t)h1;
+    m[64 + lane] = (uint16_t)h2;
+    m[96 + lane] = (uint16_t)h3;
 }
 
 // Single-search variant of one individual pattern on the staged stage, stored
@@ -475,12 +479,14 @@ __device__ __noinline__ void plain_job(const Params &P, const Header &H, Smem &S
     const uint32_t *pb = tb ? reinterpret_cast<const uint32_t *>(tb + kHashSlots) : nullptr;
     const uint64_t cf0 = (D.job.delta + 15u) / 16u, cf1 = D.job.lim / 16u;
     uint32_t h[4] = {0u, 0u, 0u, 0u};
-    bool dense = false;  // the 4-byte block variant probes every segment here
+    bool dense = false;  // the adaptive variant probes every segment here
     switch (D.variant) {  // (store_list counts the hits from the masks)
         case V_DIRECT: stage_hits<V_DIRECT, 0>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
         case V_PREFIX4: stage_hits<V_PREFIX4, 4>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
         case V_PREFIX8: stage_hits<V_PREFIX8, 8>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
-        case V_BLOCK4: stage_hits<V_BLOCK4, 4, true>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h, &dense); break;
+        case V_BLOCK4: stage_hits<V_BLOCK4, 4>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
+        case V_ADAPT: stage_hits<V_ADAPT, 4, true>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h, &dense); break;
+        case V_CODE2: stage_hits<V_CODE2, 4>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
         default: stage_hits<V_BLOCK8, 8>(D.job, cf0, cf1, Bw, tb, pb, buf, c0, w, lane, h); break;
     }
     const uint64_t st = D.stage0 + ls;

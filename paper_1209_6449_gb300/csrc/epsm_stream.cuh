@@ -46,13 +46,14 @@ constexpr int kMaxBlocksPerSm = 2;
 constexpr uint64_t kMaxBlocks = 512;                        // grid bound (range totals, status words)
 
 constexpr uint32_t kClaim = 2;                              // stages per claim
-constexpr int kBlock4Dense = 2;   // steps of 4 with a block match somewhere: use the prefix filter
-constexpr int kBlock4Epoch = 32;  // segments a warp filters with the prefix filter before it re-probes
+constexpr int kAdaptDense = 2;   // probe: steps of 4 with a block match somewhere => dense text
+constexpr int kAdaptEpoch = 32;  // segments a warp filters in the chosen mode before it re-probes
 constexpr uint64_t kEndStage = ~0ull;
 
 struct alignas(128) StreamSmem {
     uint8_t buf[kStages][kStageBuf];
     uint64_t stage_id[kStages];  // global stage held by each ring slot (kEndStage: done)
+    alignas(16) uint32_t wcnt[kStages][kConsumerWarps];  // per slot: the segments' hit counts
     uint64_t full[kStages];
     uint64_t empty[kStages];
     uint32_t pblk[16];
@@ -180,8 +181,24 @@ __device__ __forceinline__ void issue_stage(const StreamParams &P, StreamSmem &S
 // claim of the next batch is requested before the current batch is issued so
 // that its latency overlaps the copies.  When a claim comes back past the end
 // of the text, the next ring slot is marked kEndStage.
+// Publishes the counts of the stage a ring slot held, once its consumers
+// released it: the eight segment counts as two 16-byte stores, and the stage
+// total added to its range total.
+__device__ __forceinline__ void flush_slot(const StreamParams &P, StreamSmem &S, int s) {
+    const uint64_t st = S.stage_id[s];
+    const uint4 a = *reinterpret_cast<const uint4 *>(&S.wcnt[s][0]);
+    const uint4 b = *reinterpret_cast<const uint4 *>(&S.wcnt[s][4]);
+    uint4 *dst = reinterpret_cast<uint4 *>(P.seg_count + st * kConsumerWarps);
+    dst[0] = a;
+    dst[1] = b;
+    const uint32_t tot = a.x + a.y + a.z + a.w + b.x + b.y + b.z + b.w;
+    if (tot) atomicAdd(&P.range_total[st / P.range_stages], (unsigned long long)tot);
+}
+
 __device__ __forceinline__ void producer(const StreamParams &P, StreamSmem &S) {
+    static_assert(kConsumerWarps == 8, "flush_slot publishes eight counts");
     uint32_t issued = 0;
+    uint32_t pend = 0;  // bit s: slot s holds a stage whose counts are not yet published
     bool failed = false;
     uint64_t claim = atomicAdd(&P.misc->ticket, kClaim);
     for (;;) {
@@ -189,6 +206,7 @@ __device__ __forceinline__ void producer(const StreamParams &P, StreamSmem &S) {
             const int s = issued % kStages;
             const uint32_t n = issued / kStages;
             if (n > 0 && !mbar_wait(&S.empty[s], (n - 1) & 1)) { failed = true; break; }
+            if (pend >> s & 1u) { flush_slot(P, S, s); pend &= ~(1u << s); }
             S.stage_id[s] = kEndStage;
             mbar_arrive(&S.full[s]);
             ++issued;
@@ -200,7 +218,9 @@ __device__ __forceinline__ void producer(const StreamParams &P, StreamSmem &S) {
             const int s = issued % kStages;
             const uint32_t n = issued / kStages;
             if (n > 0 && !mbar_wait(&S.empty[s], (n - 1) & 1)) { failed = true; break; }
+            if (pend >> s & 1u) { flush_slot(P, S, s); pend &= ~(1u << s); }
             issue_stage(P, S, s, st);
+            if (P.emit) pend |= 1u << s;
             ++issued;
         }
         if (failed) break;
@@ -210,6 +230,17 @@ __device__ __forceinline__ void producer(const StreamParams &P, StreamSmem &S) {
     // Leave no copy in flight: wait (bounded) for the last issued stages.
     const uint32_t lo = issued > (uint32_t)kStages ? issued - kStages : 0u;
     for (uint32_t i = lo; i < issued; ++i) mbar_wait(&S.full[i % kStages], (i / kStages) & 1);
+    // Publish the counts of the stages still held: wait (bounded) until their
+    // consumers released them.
+    if (!failed) {
+        for (uint32_t i = lo; i < issued; ++i) {
+            const int s = (int)(i % kStages);
+            if (!(pend >> s & 1u)) continue;
+            if (!mbar_wait(&S.empty[s], (i / kStages) & 1)) { atomicOr(P.err, kErrTimeout); break; }
+            flush_slot(P, S, s);
+            pend &= ~(1u << s);
+        }
+    }
 }
 
 // A chunk read through the ragged-end path (its stage is not entirely inside
@@ -249,6 +280,83 @@ __device__ __forceinline__ void load_segment(const SearchJob &J, uint64_t cf0, u
 //   PROBE (4-byte block variant only): first decide from the segment whether
 //   the text is dense in block matches (`dense`), and if so filter it with
 //   the prefix filter instead.
+// The hits of one warp's segment, given its loaded chunks (lane l: chunks
+// 32u + l; lane 0 also the halo chunk after the segment).
+template <int V, int MP>
+__device__ __forceinline__ uint32_t segment_hits(const SearchJob &J, const uint4 (&ch)[4], const uint4 halo,
+                                                 int64_t sp0, bool interior, const BcastWords &B,
+                                                 const uint8_t *table, const uint32_t *pblk,
+                                                 const StagedText &T, int lane, uint32_t (&h)[4]) {
+    uint32_t cnt = 0u;
+    if constexpr (V == V_CODE2) {
+        // 2-bit code filter (Section 3.3's filter-then-verify, with the first
+        // min(m, 8) bytes of the window in the filter at two bits each): the
+        // code words of the four steps and of the halo, the next lane's by a
+        // shuffle; then, for all 16 starts of a chunk at once, the code
+        // stream shifted by j chars is XORed with the code of p_j replicated
+        // 16 times and ORed into acc, so a start survives iff its 2-bit field
+        // of acc stays zero.  Survivors are checked on the bytes in registers.
+        uint32_t C[4], Cn[4], acc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) C[u] = code2_of(ch[u]);
+        const uint32_t Ch = code2_of(halo);
+        const int src = (lane + 1) & 31;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t cs = (lane == 0) ? (u + 1 < 4 ? C[u + 1 < 4 ? u + 1 : u] : Ch) : C[u];
+            Cn[u] = __shfl_sync(kFull, cs, src);
+            acc[u] = 0u;
+        }
+        const Pattern &pat = J.pat;
+        const uint32_t pc = code2_of(make_uint4(pat.w[0], pat.w[1], pat.w[2], pat.w[3]));
+        const uint32_t mf = pat.m < 8u ? pat.m : 8u;
+#pragma unroll 1
+        for (uint32_t j = 0; j < mf; ++j) {
+            const uint32_t rep = ((pc >> (2u * j)) & 3u) * 0x55555555u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] |= __funnelshift_r(C[u], Cn[u], 2u * j) ^ rep;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t z = ~(acc[u] | (acc[u] >> 1)) & 0x55555555u;
+            uint32_t hh = 0u;
+            if (__any_sync(kFull, z != 0u)) {
+                const uint4 nsrc = (lane == 0) ? (u + 1 < 4 ? ch[u + 1 < 4 ? u + 1 : u] : halo) : ch[u];
+                const uint32_t n0 = __shfl_sync(kFull, nsrc.x, src);
+                const uint32_t n1 = __shfl_sync(kFull, nsrc.y, src);
+                const uint32_t n2 = __shfl_sync(kFull, nsrc.z, src);
+                const uint32_t n3 = __shfl_sync(kFull, nsrc.w, src);
+                if (z) hh = verify_cands_regs(pat, ch[u], n0, n1, n2, n3, even_bits(z));
+            }
+            const int64_t p0 = sp0 + (int64_t)((32 * u + lane) * 16);
+            if (!interior) hh &= range_mask((int64_t)J.delta - p0, J.pmax - p0);
+            h[u] = hh;
+            cnt += __popc(hh);
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint4 cur = ch[u];
+            const uint4 nsrc = (lane == 0) ? (u + 1 < 4 ? ch[u + 1 < 4 ? u + 1 : u] : halo) : cur;
+            const int64_t p0 = sp0 + (int64_t)((32 * u + lane) * 16);
+            uint32_t hh = chunk_hits<V, MP>(J, cur, nsrc, p0, B, table, pblk, lane, T);
+            if (!interior) hh &= range_mask((int64_t)J.delta - p0, J.pmax - p0);
+            h[u] = hh;
+            cnt += __popc(hh);
+        }
+    }
+    return cnt;
+}
+
+// Filter and verify one consumer warp's segment of a staged stage of job J:
+// the stage holds the job's chunks c0 .. c0+1024 (+ halo); lane l takes chunks
+// 32u + l of segment w.  Writes the four 16-bit hit masks to h and returns the
+// lane's hit count.
+//   V_ADAPT (PROBE only): a probe of the segment decides whether the text
+//   makes 4-byte block matches of the pattern frequent (small alphabets:
+//   most steps of the block or prefix filter would take the candidate path;
+//   *dense_out), and the segment is filtered with the 2-bit code filter if
+//   so, else with the 4-byte block filter (m >= 7) or the prefix filter.
 template <int V, int MP, bool PROBE = false>
 __device__ __forceinline__ uint32_t stage_hits(const SearchJob &J, uint64_t cf0, uint64_t cf1,
                                                const BcastWords &B, const uint8_t *table,
@@ -266,67 +374,45 @@ __device__ __forceinline__ uint32_t stage_hits(const SearchJob &J, uint64_t cf0,
     T.inside = (c0 >= cf0 && c0 + kStageChunks + 1u <= cf1) ? 1u : 0u;
     const int64_t sp0 = (int64_t)((c0 + (uint64_t)w * kSegChunks) * 16u) + OFF;
     const bool interior = sp0 >= (int64_t)J.delta && sp0 + (int64_t)(kSegChunks * 16) - 1 <= J.pmax;
-    // 4-byte block variant: a probe of the segment decides whether the text
-    // makes block matches frequent (small alphabets: most steps would take
-    // the candidate path); then the prefix filter of Section 3.3 is cheaper,
-    // with the same start offset and masks.
-    bool dense = false;
-    if constexpr (V == V_BLOCK4 && PROBE) {
-        {
-            uint32_t q0, q1, q2, q3;
-            pattern_blocks4(J.pat, q0, q1, q2, q3);
-            int steps = 0;
+    if constexpr (V == V_ADAPT) {
+        static_assert(PROBE, "the adaptive variant always probes");
+        uint32_t q0, q1, q2, q3;
+        pattern_blocks4(J.pat, q0, q1, q2, q3);
+        int steps = 0;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint4 ns = (lane == 0) ? (u + 1 < 4 ? ch[u + 1 < 4 ? u + 1 : u] : halo) : ch[u];
-                const uint32_t n0 = __shfl_sync(kFull, ns.x, (lane + 1) & 31);
-                steps += __any_sync(kFull, block4_any(ch[u], n0, q0, q1, q2, q3)) ? 1 : 0;
-            }
-            dense = steps >= kBlock4Dense;
+        for (int u = 0; u < 4; ++u) {
+            const uint4 ns = (lane == 0) ? (u + 1 < 4 ? ch[u + 1 < 4 ? u + 1 : u] : halo) : ch[u];
+            const uint32_t n0 = __shfl_sync(kFull, ns.x, (lane + 1) & 31);
+            steps += __any_sync(kFull, block4_any(ch[u], n0, q0, q1, q2, q3)) ? 1 : 0;
         }
+        const bool dense = steps >= kAdaptDense;
         *dense_out = dense;
+        if (dense) return segment_hits<V_CODE2, 4>(J, ch, halo, sp0, interior, B, table, pblk, T, lane, h);
+        if (J.pat.m >= 7u) return segment_hits<V_BLOCK4, 4>(J, ch, halo, sp0, interior, B, table, pblk, T, lane, h);
+        return segment_hits<V_PREFIX4, 4>(J, ch, halo, sp0, interior, B, table, pblk, T, lane, h);
+    } else {
+        return segment_hits<V, MP>(J, ch, halo, sp0, interior, B, table, pblk, T, lane, h);
     }
-    uint32_t cnt = 0u;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const uint4 cur = ch[u];
-        const uint4 nsrc = (lane == 0) ? (u + 1 < 4 ? ch[u + 1 < 4 ? u + 1 : u] : halo) : cur;
-        const int64_t p0 = sp0 + (int64_t)((32 * u + lane) * 16);
-        uint32_t hh;
-        if (V == V_BLOCK4 && PROBE && dense) {
-            hh = J.pat.m >= 8u ? chunk_hits<V_PREFIX8, 8>(J, cur, nsrc, p0, B, table, pblk, lane, T)
-                               : chunk_hits<V_PREFIX4, 4>(J, cur, nsrc, p0, B, table, pblk, lane, T);
-        } else {
-            hh = chunk_hits<V, MP>(J, cur, nsrc, p0, B, table, pblk, lane, T);
-        }
-        if (!interior) hh &= range_mask((int64_t)J.delta - p0, J.pmax - p0);
-        h[u] = hh;
-        cnt += __popc(hh);
-    }
-    return cnt;
 }
 
-// Per-segment results of phase 1: the count always, the lane-major packed
-// masks (lane l's four chunk masks as one 8-byte word) only if it has hits.
-__device__ __forceinline__ void store_segment(uint32_t *seg_count, uint16_t *seg_mask,
-                                              unsigned long long *range_total,
-                                              uint64_t range_stages, uint64_t st, uint64_t seg,
-                                              uint32_t cnt, const uint32_t (&h)[4], bool emit,
-                                              int lane, uint64_t &acc) {
+// Per-segment results of the filter: the count always; the 128 chunk masks,
+// in chunk order, only if the segment has hits (lane l writes chunks 32u + l).
+// The count goes to the ring slot's shared-memory row; the producer publishes
+// the stage's counts and its range total when it recycles the slot
+// (flush_slot).
+__device__ __forceinline__ void store_segment(const StreamParams &P, uint32_t *wslot, uint64_t seg,
+                                              uint32_t cnt, const uint32_t (&h)[4], int lane,
+                                              uint64_t &acc) {
     const uint32_t wc = __any_sync(kFull, cnt != 0u) ? warp_sum(cnt) : 0u;
-    if (!emit) {  // count only: the warp adds its total once, at the end
+    if (!P.emit) {  // count only: the warp adds its total once, at the end
         acc += wc;
         return;
     }
-    if (lane == 0) {
-        seg_count[seg] = wc;
-        if (wc) atomicAdd(&range_total[st / range_stages], (unsigned long long)wc);
-    }
+    if (lane == 0) *wslot = wc;
     if (wc != 0u) {
-        uint2 packed;
-        packed.x = (h[0] & 0xFFFFu) | (h[1] << 16);
-        packed.y = (h[2] & 0xFFFFu) | (h[3] << 16);
-        reinterpret_cast<uint2 *>(seg_mask + seg * kSegChunks)[lane] = packed;
+        uint16_t *m = P.seg_mask + seg * kSegChunks;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) m[32 * u + lane] = (uint16_t)h[u];
     }
 }
 
@@ -344,12 +430,11 @@ __device__ __forceinline__ bool one_segment(const StreamParams &P, StreamSmem &S
     const uint32_t cnt = stage_hits<V, MP, PROBE>(P.job, P.chunk_full0, P.chunk_full1, B, S.table,
                                                   S.pblk, S.buf[s], st * kStageChunks, w, lane, h,
                                                   dense);
+    store_segment(P, &S.wcnt[s][w], st * kConsumerWarps + (uint64_t)w, cnt, h, lane, acc);
     // the stage buffer is no longer needed: release it to the producer
     __syncwarp();
     if (lane == 0) mbar_arrive(&S.empty[s]);
     if (++s == kStages) { s = 0; phase ^= 1u; }
-    store_segment(P.seg_count, P.seg_mask, P.range_total, P.range_stages, st,
-                  st * kConsumerWarps + (uint64_t)w, cnt, h, P.emit != 0, lane, acc);
     return true;
 }
 
@@ -360,25 +445,24 @@ __device__ __forceinline__ void filter_stages(const StreamParams &P, StreamSmem 
     int s = 0;
     uint32_t phase = 0;
     uint64_t acc = 0;
-    if constexpr (V == V_BLOCK4) {
+    if constexpr (V == V_ADAPT) {
         // Epochs: one probing segment decides the mode, then the warp runs
         // that mode's own loop (no per-segment branch between the filters)
-        // until it probes again -- at once while the text stays sparse in
-        // block matches, after kBlock4Epoch segments of the prefix filter.
-        const bool p8 = P.job.pat.m >= 8u;
+        // for kAdaptEpoch segments before it probes again.
+        const bool b4 = P.job.pat.m >= 7u;
         bool more = true;
         while (more) {
             bool dense = false;
-            more = one_segment<V_BLOCK4, 4, true>(P, S, B, s, phase, w, lane, ok, acc, &dense);
+            more = one_segment<V_ADAPT, 4, true>(P, S, B, s, phase, w, lane, ok, acc, &dense);
             if (!more) break;
-            if (!dense) {
-                for (int k = 0; more && k < kBlock4Epoch; ++k)
+            if (dense) {
+                for (int k = 0; more && k < kAdaptEpoch; ++k)
+                    more = one_segment<V_CODE2, 4, false>(P, S, B, s, phase, w, lane, ok, acc, nullptr);
+            } else if (b4) {
+                for (int k = 0; more && k < kAdaptEpoch; ++k)
                     more = one_segment<V_BLOCK4, 4, false>(P, S, B, s, phase, w, lane, ok, acc, nullptr);
-            } else if (p8) {
-                for (int k = 0; more && k < kBlock4Epoch; ++k)
-                    more = one_segment<V_PREFIX8, 8, false>(P, S, B, s, phase, w, lane, ok, acc, nullptr);
             } else {
-                for (int k = 0; more && k < kBlock4Epoch; ++k)
+                for (int k = 0; more && k < kAdaptEpoch; ++k)
                     more = one_segment<V_PREFIX4, 4, false>(P, S, B, s, phase, w, lane, ok, acc, nullptr);
             }
         }
@@ -389,76 +473,40 @@ __device__ __forceinline__ void filter_stages(const StreamParams &P, StreamSmem 
     if (!P.emit && lane == 0 && acc) atomicAdd(&P.range_total[blockIdx.x % P.nranges], (unsigned long long)acc);
 }
 
-// Emit the positions of one segment (a whole warp), given lane l's packed
-// masks (chunks 32u + l, u = 0..3): bit b of the mask of chunk c is the start
-// 16*c + OFF + b.  The four per-step warp scans run interleaved; the hits are
-// staged in shared memory as offsets inside the segment, in output order, and
-// written as consecutive 8-byte positions — in one pass when they fit in the
-// 512-entry stage (the common case), else one pass per step.
+// Emit the positions of one segment (a whole warp), given its 128 chunk masks
+// in chunk order: lane l holds chunks 4l .. 4l+3 as one 64-bit word (`packed`,
+// low half first), whose bit j is the start 64l + j of the segment.  One warp
+// scan of the lanes' counts places every hit; the hits are staged in shared
+// memory as offsets inside the segment, in output order, and written as
+// consecutive 8-byte positions, 512 at a time (one window unless the
+// segment is dense).
 //   s0: the start (user coordinates) of bit 0 of the segment's first chunk.
+constexpr uint32_t kEmitWindow = 512;
 __device__ __forceinline__ void emit_segment(uint64_t *positions, uint64_t capacity, uint32_t *err,
                                              int64_t s0, uint64_t idx0, uint2 packed,
                                              uint16_t *stage, int lane) {
-    uint32_t h[4], c[4], inc[4], T[4];
-    h[0] = packed.x & 0xFFFFu;
-    h[1] = packed.x >> 16;
-    h[2] = packed.y & 0xFFFFu;
-    h[3] = packed.y >> 16;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        c[u] = __popc(h[u]);
-        inc[u] = c[u];
-    }
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint32_t t = __shfl_up_sync(kFull, inc[u], d);
-            if (lane >= d) inc[u] += t;
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) T[u] = __shfl_sync(kFull, inc[u], 31);
-    const uint32_t total = T[0] + T[1] + T[2] + T[3];
+    uint64_t mk = ((uint64_t)packed.y << 32) | (uint64_t)packed.x;
+    const uint32_t c = (uint32_t)__popcll(mk);
+    const uint32_t inc = warp_incl_scan(c, lane);
+    const uint32_t total = __shfl_sync(kFull, inc, 31);
     if (lane == 0 && idx0 + total > capacity) set_err(err, kErrCapacity);
-    if (total <= 32u * 16u) {
-        uint32_t before = 0u;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            uint32_t k = before + inc[u] - c[u];
-            uint32_t hh = h[u];
-            while (hh) {
-                const uint32_t b = (uint32_t)(__ffs(hh) - 1);
-                hh &= hh - 1u;
-                stage[k++] = (uint16_t)(u * 512 + lane * 16 + b);
-            }
-            before += T[u];
+    const uint32_t pos0 = (uint32_t)lane * 64u;
+    uint32_t k = inc - c;  // the lane's next output index inside the segment
+    for (uint32_t w0 = 0; w0 < total; w0 += kEmitWindow) {
+        const uint32_t w1 = w0 + kEmitWindow;
+        while (mk != 0ull && k < w1) {
+            const uint32_t b = (uint32_t)(__ffsll((long long)mk) - 1);
+            mk &= mk - 1ull;
+            stage[k - w0] = (uint16_t)(pos0 + b);
+            ++k;
         }
         __syncwarp();
-        for (uint32_t q = lane; q < total; q += 32u) {
-            const uint64_t idx = idx0 + q;
+        const uint32_t nw = total - w0 < kEmitWindow ? total - w0 : kEmitWindow;
+        for (uint32_t q = lane; q < nw; q += 32u) {
+            const uint64_t idx = idx0 + w0 + q;
             if (idx < capacity) positions[idx] = (uint64_t)(s0 + stage[q]);
         }
         __syncwarp();
-        return;
-    }
-    uint32_t run = 0u;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        uint32_t k = inc[u] - c[u];
-        uint32_t hh = h[u];
-        while (hh) {
-            const uint32_t b = (uint32_t)(__ffs(hh) - 1);
-            hh &= hh - 1u;
-            stage[k++] = (uint16_t)(u * 512 + lane * 16 + b);
-        }
-        __syncwarp();
-        for (uint32_t q = lane; q < T[u]; q += 32u) {
-            const uint64_t idx = idx0 + run + q;
-            if (idx < capacity) positions[idx] = (uint64_t)(s0 + stage[q]);
-        }
-        __syncwarp();
-        run += T[u];
     }
 }
 

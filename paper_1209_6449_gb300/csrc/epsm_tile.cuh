@@ -134,21 +134,11 @@ __device__ __forceinline__ bool verify_all_regs(const uint32_t (&RR)[8], uint32_
     return ok;
 }
 
-// 4-byte block variant, slow path: a word k of the chunk (k = 0..3) or the
-// next chunk's first word (k = 4) equals a pattern block p[j..j+3] (q[j]); the
-// match gives the candidate start 4k - j when it lies in the chunk
-// (0 <= 4k - j <= 15), which is then checked in full in registers.
-__device__ __noinline__ uint32_t block4_candidates(const Pattern &pat, const uint4 cur, uint32_t n0,
+// Full in-register check of the candidate starts `cand` (bits 0..15) of a
+// chunk, given the chunk's words and the next chunk's (m <= 16).
+__device__ __noinline__ uint32_t verify_cands_regs(const Pattern &pat, const uint4 cur, uint32_t n0,
                                                    uint32_t n1, uint32_t n2, uint32_t n3,
-                                                   uint32_t q0, uint32_t q1, uint32_t q2, uint32_t q3) {
-    const uint32_t R[5] = {cur.x, cur.y, cur.z, cur.w, n0};
-    const uint32_t q[4] = {q0, q1, q2, q3};
-    uint32_t cand = 0u;
-#pragma unroll
-    for (int k = 0; k < 5; ++k)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (4 * k - j >= 0 && 4 * k - j <= 15 && R[k] == q[j]) cand |= 1u << (4 * k - j);
+                                                   uint32_t cand) {
     const uint32_t RR[8] = {cur.x, cur.y, cur.z, cur.w, n0, n1, n2, n3};
     uint32_t h = 0u;
     while (cand) {
@@ -164,6 +154,48 @@ __device__ __noinline__ uint32_t block4_candidates(const Pattern &pat, const uin
         if (ok) h |= 1u << i;
     }
     return h;
+}
+
+// 2-bit code variant (m <= 16): every byte is reduced to its bits 1 and 2
+// (a code that tells A, C, G and T apart, upper or lower case), so the 16
+// bytes of a chunk give one 32-bit code word, char i at bits 2i..2i+1.  One
+// multiply gathers the four codes of a word into its top byte (the partial
+// products land on disjoint bits, so no carries), three byte permutes
+// assemble the chunk's word.
+__device__ __forceinline__ uint32_t code2_of(const uint4 c) {
+    const uint32_t px = ((c.x >> 1) & 0x03030303u) * 0x01041040u;
+    const uint32_t py = ((c.y >> 1) & 0x03030303u) * 0x01041040u;
+    const uint32_t pz = ((c.z >> 1) & 0x03030303u) * 0x01041040u;
+    const uint32_t pw = ((c.w >> 1) & 0x03030303u) * 0x01041040u;
+    const uint32_t lo = __byte_perm(px, py, 0x0073u);  // bytes 0, 1: px.b3, py.b3
+    const uint32_t hi = __byte_perm(pz, pw, 0x7300u);  // bytes 2, 3: pz.b3, pw.b3
+    return __byte_perm(lo, hi, 0x7610u);
+}
+
+// Bits 0, 2, .., 30 of z gathered into bits 0..15.
+__device__ __forceinline__ uint32_t even_bits(uint32_t z) {
+    z = (z | (z >> 1)) & 0x33333333u;
+    z = (z | (z >> 2)) & 0x0F0F0F0Fu;
+    z = (z | (z >> 4)) & 0x00FF00FFu;
+    return (z | (z >> 8)) & 0x0000FFFFu;
+}
+
+// 4-byte block variant, slow path: a word k of the chunk (k = 0..3) or the
+// next chunk's first word (k = 4) equals a pattern block p[j..j+3] (q[j]); the
+// match gives the candidate start 4k - j when it lies in the chunk
+// (0 <= 4k - j <= 15), which is then checked in full in registers.
+__device__ __noinline__ uint32_t block4_candidates(const Pattern &pat, const uint4 cur, uint32_t n0,
+                                                   uint32_t n1, uint32_t n2, uint32_t n3,
+                                                   uint32_t q0, uint32_t q1, uint32_t q2, uint32_t q3) {
+    const uint32_t R[5] = {cur.x, cur.y, cur.z, cur.w, n0};
+    const uint32_t q[4] = {q0, q1, q2, q3};
+    uint32_t cand = 0u;
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (4 * k - j >= 0 && 4 * k - j <= 15 && R[k] == q[j]) cand |= 1u << (4 * k - j);
+    return verify_cands_regs(pat, cur, n0, n1, n2, n3, cand);
 }
 
 // The four pattern blocks p[j..j+3], j = 0..3, of the 4-byte block variant.

@@ -37,6 +37,8 @@ VARIANTS = {  # variant -> covered m
     3: range(8, 16),
     4: range(15, 33),
     5: range(7, 17),
+    6: range(2, 17),
+    7: range(5, 17),
 }
 
 
