@@ -47,13 +47,13 @@ constexpr uint64_t kMaxBlocks = 512;                        // grid bound (range
 
 constexpr uint32_t kClaim = 2;                              // stages per claim
 constexpr int kAdaptDense = 2;   // probe: steps of 4 with a block match somewhere => dense text
-constexpr int kAdaptEpoch = 32;  // segments a warp filters in the chosen mode before it re-probes
 constexpr uint64_t kEndStage = ~0ull;
 
 struct alignas(128) StreamSmem {
     uint8_t buf[kStages][kStageBuf];
     uint64_t stage_id[kStages];  // global stage held by each ring slot (kEndStage: done)
     alignas(16) uint32_t wcnt[kStages][kConsumerWarps];  // per slot: the segments' hit counts
+    uint32_t votes;              // adaptive variant: consumer warps whose probe found dense text
     uint64_t full[kStages];
     uint64_t empty[kStages];
     uint32_t pblk[16];
@@ -308,13 +308,12 @@ __device__ __forceinline__ uint32_t segment_hits(const SearchJob &J, const uint4
             acc[u] = 0u;
         }
         const Pattern &pat = J.pat;
-        const uint32_t pc = code2_of(make_uint4(pat.w[0], pat.w[1], pat.w[2], pat.w[3]));
-        const uint32_t mf = pat.m < 8u ? pat.m : 8u;
-#pragma unroll 1
-        for (uint32_t j = 0; j < mf; ++j) {
-            const uint32_t rep = ((pc >> (2u * j)) & 3u) * 0x55555555u;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) acc[u] |= __funnelshift_r(C[u], Cn[u], 2u * j) ^ rep;
+        for (int j = 0; j < 8; ++j) {
+            if ((uint32_t)j < pat.m) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] |= __funnelshift_r(C[u], Cn[u], 2 * j) ^ B.r2[j];
+            }
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -446,24 +445,25 @@ __device__ __forceinline__ void filter_stages(const StreamParams &P, StreamSmem 
     uint32_t phase = 0;
     uint64_t acc = 0;
     if constexpr (V == V_ADAPT) {
-        // Epochs: one probing segment decides the mode, then the warp runs
-        // that mode's own loop (no per-segment branch between the filters)
-        // for kAdaptEpoch segments before it probes again.
-        const bool b4 = P.job.pat.m >= 7u;
-        bool more = true;
-        while (more) {
-            bool dense = false;
-            more = one_segment<V_ADAPT, 4, true>(P, S, B, s, phase, w, lane, ok, acc, &dense);
-            if (!more) break;
-            if (dense) {
-                for (int k = 0; more && k < kAdaptEpoch; ++k)
-                    more = one_segment<V_CODE2, 4, false>(P, S, B, s, phase, w, lane, ok, acc, nullptr);
-            } else if (b4) {
-                for (int k = 0; more && k < kAdaptEpoch; ++k)
-                    more = one_segment<V_BLOCK4, 4, false>(P, S, B, s, phase, w, lane, ok, acc, nullptr);
+        // The consumer warps probe their first segments (one stage of the
+        // text) and the block takes the majority: the code filter for the
+        // block's whole run where the text is dense in block matches, else
+        // the 4-byte block filter (m >= 7) or the prefix filter.  One mode
+        // per block keeps each loop as tight as the plain variant's.
+        bool dense = false;
+        const bool more = one_segment<V_ADAPT, 4, true>(P, S, B, s, phase, w, lane, ok, acc, &dense);
+        if (lane == 0 && dense) atomicAdd(&S.votes, 1u);
+        consumer_sync();  // every consumer warp gets here, whatever its first segment did
+        if (more) {
+            if (S.votes * 2u >= (uint32_t)kConsumerWarps) {
+                while (one_segment<V_CODE2, 4, false>(P, S, B, s, phase, w, lane, ok, acc, nullptr)) {
+                }
+            } else if (P.job.pat.m >= 7u) {
+                while (one_segment<V_BLOCK4, 4, false>(P, S, B, s, phase, w, lane, ok, acc, nullptr)) {
+                }
             } else {
-                for (int k = 0; more && k < kAdaptEpoch; ++k)
-                    more = one_segment<V_PREFIX4, 4, false>(P, S, B, s, phase, w, lane, ok, acc, nullptr);
+                while (one_segment<V_PREFIX4, 4, false>(P, S, B, s, phase, w, lane, ok, acc, nullptr)) {
+                }
             }
         }
     } else {
@@ -636,6 +636,7 @@ __global__ void __launch_bounds__(stream::kThreadsStream, stream::kMaxBlocksPerS
             mbar_init(&S.full[s], 1);
             mbar_init(&S.empty[s], kConsumerWarps);
         }
+        S.votes = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // S1: pattern preprocessing (block fingerprint table, Section 3.4)

@@ -38,9 +38,13 @@ __device__ __forceinline__ void build_block_table(const Pattern &pat, uint8_t *t
 // Broadcast words (p_j)^4 of the first eight pattern bytes (Section 3.2, table B).
 struct BcastWords {
     uint32_t b[8];
+    uint32_t r2[8];  // the 2-bit code of p_j replicated 16 times (2-bit code variant)
     __device__ __forceinline__ explicit BcastWords(const Pattern &pat) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) b[j] = bcast_byte(pat.w[j >> 2], j & 3);
+        for (int j = 0; j < 8; ++j) {
+            b[j] = bcast_byte(pat.w[j >> 2], j & 3);
+            r2[j] = ((b[j] >> 1) & 0x03030303u) * 0x55u;
+        }
     }
 };
 
@@ -163,10 +167,11 @@ __device__ __noinline__ uint32_t verify_cands_regs(const Pattern &pat, const uin
 // products land on disjoint bits, so no carries), three byte permutes
 // assemble the chunk's word.
 __device__ __forceinline__ uint32_t code2_of(const uint4 c) {
-    const uint32_t px = ((c.x >> 1) & 0x03030303u) * 0x01041040u;
-    const uint32_t py = ((c.y >> 1) & 0x03030303u) * 0x01041040u;
-    const uint32_t pz = ((c.z >> 1) & 0x03030303u) * 0x01041040u;
-    const uint32_t pw = ((c.w >> 1) & 0x03030303u) * 0x01041040u;
+    // (c & 0x06..) * 0x00820820 == ((c >> 1) & 0x03..) * 0x01041040
+    const uint32_t px = (c.x & 0x06060606u) * 0x00820820u;
+    const uint32_t py = (c.y & 0x06060606u) * 0x00820820u;
+    const uint32_t pz = (c.z & 0x06060606u) * 0x00820820u;
+    const uint32_t pw = (c.w & 0x06060606u) * 0x00820820u;
     const uint32_t lo = __byte_perm(px, py, 0x0073u);  // bytes 0, 1: px.b3, py.b3
     const uint32_t hi = __byte_perm(pz, pw, 0x7300u);  // bytes 2, 3: pz.b3, pw.b3
     return __byte_perm(lo, hi, 0x7610u);
