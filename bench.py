@@ -56,8 +56,9 @@ def parse():
     ap.add_argument("--patterns", type=int, default=PATS_PER_M,
                     help="patterns per (text, m); the workload uses 100")
     ap.add_argument("--case", default=None,
-                    help="KIND:M[:VARIANT[:N]] — time one search of an N-byte text "
-                         "(default 256 MiB) and exit (the small case used for ncu captures)")
+                    help="KIND:M[:VARIANT[:N[:count]]] — time one search of an N-byte text "
+                         "(default 256 MiB; 'count': count only) and exit (the small case "
+                         "used for ncu captures)")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--sample", action="store_true",
                     help="one search per (text, m) of the sweep (15 launches) and exit; the "
@@ -83,12 +84,13 @@ def run_case(args):
     kind, m = parts[0], int(parts[1])
     variant = int(parts[2]) if len(parts) > 2 else 0
     n = int(parts[3]) if len(parts) > 3 else TEXT_N
+    count_only = len(parts) > 4 and parts[4] == "count"
     ctx = epsm.Context(0)
     t = torch.empty(n, dtype=torch.uint8, device="cuda")
     gen.TextSpec(kind, 0).device(n, t.data_ptr(), torch.cuda.current_stream().cuda_stream)
     pat = gen.planted_patterns(gen.TextSpec(kind, 0), n, m, 1)[0]
-    cap = n // 3
-    out = torch.empty(cap, dtype=torch.int64, device="cuda")
+    cap = 0 if count_only else n // 3
+    out = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     times = []
     for _ in range(args.reps):
