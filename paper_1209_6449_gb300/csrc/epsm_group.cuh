@@ -436,8 +436,8 @@ __device__ __noinline__ void store_short_list(const Params &P, const Header &H, 
 // Phase-1 result of one pattern segment (a whole warp; lane l holds the hit
 // masks of chunks 32u + l): the count, added to its emit range's total, and,
 // when positions are wanted, in the warp's current pool chunk either its 128
-// chunk masks (at least kMaskMin hits: lane-major, lane l's four masks as one
-// 8-byte word) or the sorted list of its hit offsets (chunk * 16 + bit).
+// chunk masks in chunk order (at least kMaskMin hits) or the sorted list of
+// its hit offsets (chunk * 16 + bit).
 __device__ __forceinline__ void store_list(const Params &P, const Header &H, Smem &S, uint64_t st,
                                            uint64_t seg, uint32_t h0, uint32_t h1, uint32_t h2,
                                            uint32_t h3, int w, int lane) {
