@@ -12,7 +12,10 @@
  * fingerprint filter plus verify for medium patterns) as sm_103a kernels.
  *
  * Conventions for every entry point:
- *   - 1 <= m <= EPSM_MAX_M (32); m == 0 or m > 32 returns EPSM_ERR_ARG.
+ *   - 1 <= m <= EPSM_MAX_M (32); m == 0 or m > 32 returns EPSM_ERR_ARG, except
+ *     that the single-search entry points (epsm_search, epsm_search_async,
+ *     epsm_search_variant with EPSM_VARIANT_AUTO or EPSM_VARIANT_BLOCK8) take
+ *     m up to EPSM_MAX_M_LONG (4096).
  *   - m > n is not an error: the count is 0.
  *   - Inputs are never modified.  Buffers named "device" must be device
  *     memory of the context's device (or managed memory); buffers named "host"
@@ -40,6 +43,10 @@ extern "C" {
 #endif
 
 #define EPSM_MAX_M 32u
+/* Longest pattern of the single-search entry points (epsm_search,
+ * epsm_search_async, epsm_search_variant): m > EPSM_MAX_M uses the 8-byte
+ * block variant on the first 32 bytes and checks the rest at each candidate. */
+#define EPSM_MAX_M_LONG 4096u
 
 typedef struct epsm_ctx epsm_ctx;
 

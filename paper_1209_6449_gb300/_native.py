@@ -18,6 +18,7 @@ STATUS_NAMES = ["EPSM_OK", "EPSM_ERR_ARG", "EPSM_ERR_CAPACITY", "EPSM_ERR_CUDA",
  VARIANT_ADAPT) = range(8)
 VARIANT_NAMES = {1: "direct", 2: "prefix4", 3: "prefix8", 4: "block8", 5: "block4", 6: "code2", 7: "adapt"}
 MAX_M = 32
+MAX_M_LONG = 4096  # single-search entry points only
 
 EXPORTS = ["epsm_create", "epsm_destroy", "epsm_status_str", "epsm_last_error",
            "epsm_search", "epsm_search_async", "epsm_search_variant", "epsm_sync",

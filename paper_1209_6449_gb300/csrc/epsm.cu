@@ -150,6 +150,9 @@ struct epsm_ctx {
     uint64_t dtext_cap = 0;
     uint64_t *dpos = nullptr;
     uint64_t dpos_cap = 0;
+    // pattern bytes past the first 32 of a long pattern (m > EPSM_MAX_M)
+    uint8_t *tail = nullptr;
+    uint32_t tail_cap = 0;
 };
 
 namespace {
@@ -289,11 +292,14 @@ epsm_status search_async_impl(epsm_ctx *c, int variant, const uint8_t *text, uin
                               uint64_t capacity, uint64_t *count_dev, void *stream,
                               int64_t pos_bias) {
     if (!c || !pattern || !count_dev) return EPSM_ERR_ARG;
-    if (m == 0 || m > EPSM_MAX_M) return EPSM_ERR_ARG;
+    if (m == 0 || m > EPSM_MAX_M_LONG) return EPSM_ERR_ARG;
     if (n > 0 && !text) return EPSM_ERR_ARG;
     if (capacity > 0 && !positions) return EPSM_ERR_ARG;
-    int v = variant == EPSM_VARIANT_AUTO ? c->variant[m] : variant;
-    if (!variant_covers(v, m)) return EPSM_ERR_ARG;
+    // a long pattern: the 8-byte block filter and check on its first 32
+    // bytes, then the rest of the pattern checked at each candidate
+    const bool longp = m > EPSM_MAX_M;
+    int v = variant == EPSM_VARIANT_AUTO ? (longp ? V_BLOCK8 : c->variant[m]) : variant;
+    if (!(longp ? v == V_BLOCK8 : variant_covers(v, m))) return EPSM_ERR_ARG;
     cudaStream_t s = pick_stream(c, stream);
     epsm_status st = order_after_previous(c, s);
     if (st != EPSM_OK) return st;
@@ -303,7 +309,23 @@ epsm_status search_async_impl(epsm_ctx *c, int variant, const uint8_t *text, uin
     }
     stream::StreamParams p;
     memset(&p, 0, sizeof(p));
-    p.job = make_job(text, n, pack_pattern(pattern, m));
+    p.job = make_job(text, n, pack_pattern(pattern, longp ? EPSM_MAX_M : m));
+    if (longp) {
+        p.job.pmax = (int64_t)(p.job.delta + n) - (int64_t)m;
+        const uint32_t mt = m - EPSM_MAX_M;
+        if (mt > c->tail_cap) {
+            CK(cudaStreamSynchronize(s));
+            if (c->tail) CK(cudaFree(c->tail));
+            c->tail = nullptr;
+            c->tail_cap = 0;
+            CK(cudaMalloc(&c->tail, EPSM_MAX_M_LONG));
+            c->tail_cap = EPSM_MAX_M_LONG;
+        }
+        // from pageable host memory: the source is consumed before the call returns
+        CK(cudaMemcpyAsync(c->tail, pattern + EPSM_MAX_M, mt, cudaMemcpyHostToDevice, s));
+        p.tail = c->tail;
+        p.mtail = mt;
+    }
     p.nstages = stages_for(p.job.delta, n, m, v);
     p.chunk_full0 = (p.job.delta + 15u) / 16u;
     p.chunk_full1 = p.job.lim / 16u;
@@ -850,6 +872,7 @@ EPSM_API epsm_status epsm_destroy(epsm_ctx *c) {
     if (c->seg_mask) cudaFree(c->seg_mask);
     if (c->dtext) cudaFree(c->dtext);
     if (c->dpos) cudaFree(c->dpos);
+    if (c->tail) cudaFree(c->tail);
     if (c->ev) cudaEventDestroy(c->ev);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;

@@ -187,7 +187,19 @@ struct StagedText {
     int64_t sbase;
     uint32_t span;
     uint32_t inside;
+    const uint8_t *tail;  // a long pattern's bytes past its first 32 (global), else null
+    uint32_t mtail;
 };
+
+// The bytes of a long pattern past its first 32 (tail[0..len)) against the
+// text at internal position P (inside the text: P + len <= lim), from global
+// memory.
+__device__ __noinline__ bool verify_tail(const SearchJob &J, int64_t P, const uint8_t *tail,
+                                         uint32_t len) {
+    for (uint32_t i = 0; i < len; ++i)
+        if (ldg_u8(J.base + P + i) != ldg_u8(tail + i)) return false;
+    return true;
+}
 
 // t[P..P+m) == p, read from the staged bytes when they cover it (shared
 // memory word loads), else from global memory.

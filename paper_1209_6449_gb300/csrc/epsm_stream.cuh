@@ -146,6 +146,8 @@ struct StreamParams {
     uint64_t chunk_full0;  // first chunk lying fully inside [delta, lim)
     uint64_t chunk_full1;  // one past the last such chunk
     int emit;              // 0: count only
+    const uint8_t *tail;   // long pattern (m > 32, block variant): its bytes past the first 32
+    uint32_t mtail;        // their number (0: none)
 };
 
 // Chunk c of job J as staged in `buf` (the stage's first chunk is c0), or read
@@ -361,7 +363,8 @@ __device__ __forceinline__ uint32_t stage_hits(const SearchJob &J, uint64_t cf0,
                                                const BcastWords &B, const uint8_t *table,
                                                const uint32_t *pblk, const uint8_t *buf,
                                                uint64_t c0, int w, int lane, uint32_t (&h)[4],
-                                               bool *dense_out = nullptr) {
+                                               bool *dense_out = nullptr, const uint8_t *tail = nullptr,
+                                               uint32_t mtail = 0u) {
     constexpr int OFF = (V == V_BLOCK8) ? -7 : 0;
     uint4 ch[4];
     uint4 halo;
@@ -371,6 +374,8 @@ __device__ __forceinline__ uint32_t stage_hits(const SearchJob &J, uint64_t cf0,
     T.sbase = (int64_t)(c0 * 16u);
     T.span = (uint32_t)((kStageChunks + 1) * 16);
     T.inside = (c0 >= cf0 && c0 + kStageChunks + 1u <= cf1) ? 1u : 0u;
+    T.tail = tail;
+    T.mtail = mtail;
     const int64_t sp0 = (int64_t)((c0 + (uint64_t)w * kSegChunks) * 16u) + OFF;
     const bool interior = sp0 >= (int64_t)J.delta && sp0 + (int64_t)(kSegChunks * 16) - 1 <= J.pmax;
     if constexpr (V == V_ADAPT) {
@@ -428,7 +433,7 @@ __device__ __forceinline__ bool one_segment(const StreamParams &P, StreamSmem &S
     uint32_t h[4];
     const uint32_t cnt = stage_hits<V, MP, PROBE>(P.job, P.chunk_full0, P.chunk_full1, B, S.table,
                                                   S.pblk, S.buf[s], st * kStageChunks, w, lane, h,
-                                                  dense);
+                                                  dense, P.tail, P.mtail);
     store_segment(P, &S.wcnt[s][w], st * kConsumerWarps + (uint64_t)w, cnt, h, lane, acc);
     // the stage buffer is no longer needed: release it to the producer
     __syncwarp();

@@ -117,7 +117,9 @@ __device__ __noinline__ uint32_t block_candidates(const SearchJob &J, const uint
         int i = __ffs(cand) - 1;
         cand &= cand - 1u;
         int64_t P = p0 + i;
-        if (P >= (int64_t)J.delta && P <= J.pmax && verify_staged(J, P, T)) h |= 1u << i;
+        if (P >= (int64_t)J.delta && P <= J.pmax && verify_staged(J, P, T) &&
+            (T.mtail == 0u || verify_tail(J, P + 32, T.tail, T.mtail)))
+            h |= 1u << i;
     }
     return h;
 }

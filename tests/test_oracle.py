@@ -154,3 +154,26 @@ def test_paper_procedures_periodic():
         for m in range(1, 33):
             want = list(range(n - m + 1)) if m <= n else []
             assert sorted(paper.epsm(b"A" * m, t)) == want
+
+
+def test_long_patterns_pinned():
+    """Long patterns (32 < m <= 4096, single search): the closed form a^m in
+    a^n, the periodic (ab)^k family, and planted occurrences over a disjoint
+    alphabet pin the oracle beyond m = 32."""
+    for m in (33, 100, 4096):
+        n = 5000
+        text = np.full(n, 0x61, dtype=np.uint8)
+        assert np.array_equal(oracle.search(text, b"a" * m), np.arange(n - m + 1, dtype=np.uint64))
+    text = np.frombuffer(b"ab" * 3000, dtype=np.uint8)
+    for k in (17, 40):
+        got = oracle.search(text, b"ab" * k)
+        assert np.array_equal(got, np.arange(0, 6000 - 2 * k + 1, 2, dtype=np.uint64))
+        got = oracle.search(text, b"ba" * k)  # odd starts 1 .. 6000 - 2k - 1
+        assert np.array_equal(got, np.arange(1, 6000 - 2 * k, 2, dtype=np.uint64))
+    rng = np.random.default_rng(7)
+    text = rng.integers(0, 4, size=1 << 16).astype(np.uint8)  # bytes 0..3
+    pat = bytes(range(100, 100 + 60))  # disjoint from the text's bytes
+    starts = [5, 1000, 1060, 40000]
+    for s in starts:
+        text[s:s + len(pat)] = np.frombuffer(pat, dtype=np.uint8)
+    assert list(oracle.search(text, pat)) == starts

@@ -159,7 +159,8 @@ def test_bad_arguments(ctx, torch, epsm):
     s = torch.cuda.current_stream().cuda_stream
     assert epsm.epsm_search_async(h, dev.data_ptr(), 100, b"", 0, out.data_ptr(), 4,
                                   cnt.data_ptr(), s) == 1
-    assert epsm.epsm_search_async(h, dev.data_ptr(), 100, b"a" * 33, 33, out.data_ptr(), 4,
+    big = epsm.MAX_M_LONG + 1  # the single search takes m up to MAX_M_LONG
+    assert epsm.epsm_search_async(h, dev.data_ptr(), 100, b"a" * big, big, out.data_ptr(), 4,
                                   cnt.data_ptr(), s) == 1
     # a variant that does not cover m
     assert epsm.epsm_search_variant(h, 4, dev.data_ptr(), 100, b"abc", 3, out.data_ptr(), 4,
