@@ -327,7 +327,14 @@ __device__ __forceinline__ uint32_t segment_hits(const SearchJob &J, const uint4
                 const uint32_t n1 = __shfl_sync(kFull, nsrc.y, src);
                 const uint32_t n2 = __shfl_sync(kFull, nsrc.z, src);
                 const uint32_t n3 = __shfl_sync(kFull, nsrc.w, src);
-                if (z) hh = verify_cands_regs(pat, ch[u], n0, n1, n2, n3, even_bits(z));
+                const uint32_t cand = z ? even_bits(z) : 0u;
+                if (__any_sync(kFull, __popc(cand) > 3)) {
+                    // many candidates somewhere in the warp (a run of one
+                    // byte): all 16 starts checked at once on the bytes
+                    hh = cand ? exact_chunk_regs(pat, ch[u], n0, n1, n2, n3) & cand : 0u;
+                } else if (cand) {
+                    hh = verify_cands_regs(pat, ch[u], n0, n1, n2, n3, cand);
+                }
             }
             const int64_t p0 = sp0 + (int64_t)((32 * u + lane) * 16);
             if (!interior) hh &= range_mask((int64_t)J.delta - p0, J.pmax - p0);

@@ -99,10 +99,45 @@ __device__ __forceinline__ uint32_t verify_word_hits(uint32_t z, const uint32_t 
     return h;
 }
 
+// Exact check of all 16 starts of a chunk at once, for chunks with many
+// candidates (runs of one byte and the like), given the text as words R[0..]
+// aligned to the chunk's first start (R must hold 16 + m - 1 bytes): for every
+// pattern byte j the shifted text words are XORed with (p_j)^4 and ORed into
+// one mismatch word per 4 starts, whose zero bytes are the hits (the
+// packed compare of Section 3.2 extended to every j < m).
+template <int NW>
+__device__ __forceinline__ uint32_t exact_starts16(const uint32_t (&R)[NW], const Pattern &pat) {
+    static_assert(NW >= 5 && NW <= 12, "16 starts and up to 32 pattern bytes");
+    uint32_t acc0 = 0u, acc1 = 0u, acc2 = 0u, acc3 = 0u;
+    const uint32_t m = pat.m;
+#pragma unroll
+    for (int j = 0; j < 4 * (NW - 4); ++j) {
+        if ((uint32_t)j < m) {
+            const uint32_t b = bcast_byte(pat.w[j >> 2], j & 3);
+            const int q = j >> 2, sh = 8 * (j & 3);
+            acc0 |= (sh ? __funnelshift_r(R[q], R[q + 1], sh) : R[q]) ^ b;
+            acc1 |= (sh ? __funnelshift_r(R[q + 1], R[q + 2], sh) : R[q + 1]) ^ b;
+            acc2 |= (sh ? __funnelshift_r(R[q + 2], R[q + 3], sh) : R[q + 2]) ^ b;
+            acc3 |= (sh ? __funnelshift_r(R[q + 3], R[q + 4], sh) : R[q + 3]) ^ b;
+        }
+    }
+    return nibble_of(zero_bytes(acc0)) | (nibble_of(zero_bytes(acc1)) << 4) |
+           (nibble_of(zero_bytes(acc2)) << 8) | (nibble_of(zero_bytes(acc3)) << 12);
+}
+
+// exact_starts16 on the bytes of a chunk and the next chunk (m <= 16); out
+// of line, so the filter loops that rarely call it keep their registers.
+__device__ __noinline__ uint32_t exact_chunk_regs(const Pattern &pat, const uint4 cur, uint32_t n0,
+                                                  uint32_t n1, uint32_t n2, uint32_t n3) {
+    const uint32_t R[8] = {cur.x, cur.y, cur.z, cur.w, n0, n1, n2, n3};
+    return exact_starts16<8>(R, pat);
+}
+
 // Block variant, slow path: one of the chunk's two blocks hit a marked
 // fingerprint slot.  Compare the blocks with the pattern blocks p[j..j+7]; a
 // block match at j gives the candidate 8b - j, which is checked in full.
-__device__ __noinline__ uint32_t block_candidates(const SearchJob &J, const uint4 cur, int64_t p0,
+// (Inlined: an out-of-line call in the filter loop costs it about 10%.)
+__device__ __forceinline__ uint32_t block_candidates(const SearchJob &J, const uint4 cur, int64_t p0,
                                                   const uint32_t *pblk, uint32_t t0, uint32_t t1,
                                                   const StagedText &T) {
     uint32_t cand = 0u;
