@@ -252,13 +252,27 @@ cudaError_t launch_stream_t(int sms, stream::StreamParams &p, cudaStream_t s) {
     p.range_stages = (nst + want - 1) / want;
     p.nranges = (uint32_t)((nst + p.range_stages - 1) / p.range_stages);
     p.off = variant_offset(V);
-    stream_kernel<V, MP><<<(unsigned)grid, stream::kThreadsStream, smem, s>>>(p);
-    cudaError_t e = cudaGetLastError();
+    // both kernels are launched as programmatic dependents of the previous
+    // kernel of the stream: each waits on the device (grid_dep_wait) for its
+    // predecessor to finish, so their launch latency overlaps the predecessor
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(stream::kThreadsStream);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, stream_kernel<V, MP>, p);
     if (e != cudaSuccess || !p.emit) return e;
     const int eg = stream_emit_grid(sms);
     if (eg == 0) return cudaErrorUnknown;
-    stream_emit_kernel<<<(unsigned)eg, stream::kEmitThreads, 0, s>>>(p);
-    return cudaGetLastError();
+    cfg.gridDim = dim3((unsigned)eg);
+    cfg.blockDim = dim3(stream::kEmitThreads);
+    cfg.dynamicSmemBytes = 0;
+    return cudaLaunchKernelEx(&cfg, stream_emit_kernel, p);
 }
 
 cudaError_t launch_stream(int sms, int v, uint32_t m, stream::StreamParams &p,

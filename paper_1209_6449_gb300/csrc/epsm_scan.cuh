@@ -120,6 +120,16 @@ __device__ __forceinline__ uint32_t load_word(const SearchJob &J, uint64_t widx)
     return w;
 }
 
+// Programmatic dependent launch (kernels launched with the programmatic
+// stream serialization attribute may start before the previous kernel of the
+// stream ends): wait until that kernel has completed and its writes are
+// visible (returns at once when there is none), and let the next kernel be
+// scheduled (it waits for this one in the same way before it reads anything).
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Sets an error bit; reads first so that many reporters of the same
 // condition do not all queue an atomic on one word.
 __device__ __forceinline__ void set_err(uint32_t *err, uint32_t bit) {

@@ -488,12 +488,14 @@ __device__ __forceinline__ void filter_stages(const StreamParams &P, StreamSmem 
 // Emit the positions of one segment (a whole warp), given its 128 chunk masks
 // in chunk order: lane l holds chunks 4l .. 4l+3 as one 64-bit word (`packed`,
 // low half first), whose bit j is the start 64l + j of the segment.  One warp
-// scan of the lanes' counts places every hit; the hits are staged in shared
+// scan of the lanes' counts places every hit.  A segment with few hits has
+// each lane store its own positions; otherwise the hits are staged in shared
 // memory as offsets inside the segment, in output order, and written as
 // consecutive 8-byte positions, 512 at a time (one window unless the
 // segment is dense).
 //   s0: the start (user coordinates) of bit 0 of the segment's first chunk.
 constexpr uint32_t kEmitWindow = 512;
+constexpr uint32_t kEmitDirect = 64;  // segments with at most this many hits skip the staging
 __device__ __forceinline__ void emit_segment(uint64_t *positions, uint64_t capacity, uint32_t *err,
                                              int64_t s0, uint64_t idx0, uint2 packed,
                                              uint16_t *stage, int lane) {
@@ -504,6 +506,16 @@ __device__ __forceinline__ void emit_segment(uint64_t *positions, uint64_t capac
     if (lane == 0 && idx0 + total > capacity) set_err(err, kErrCapacity);
     const uint32_t pos0 = (uint32_t)lane * 64u;
     uint32_t k = inc - c;  // the lane's next output index inside the segment
+    if (total <= kEmitDirect) {
+        // few hits: each lane writes its own (at most a few) positions
+        while (mk != 0ull) {
+            const uint32_t b = (uint32_t)(__ffsll((long long)mk) - 1);
+            mk &= mk - 1ull;
+            const uint64_t idx = idx0 + k++;
+            if (idx < capacity) positions[idx] = (uint64_t)(s0 + (int64_t)(pos0 + b));
+        }
+        return;
+    }
     for (uint32_t w0 = 0; w0 < total; w0 += kEmitWindow) {
         const uint32_t w1 = w0 + kEmitWindow;
         while (mk != 0ull && k < w1) {
@@ -653,6 +665,10 @@ __global__ void __launch_bounds__(stream::kThreadsStream, stream::kMaxBlocksPerS
     }
     // S1: pattern preprocessing (block fingerprint table, Section 3.4)
     if (V == V_BLOCK8) build_block_table(P.job.pat, S.table, S.pblk);
+    // the previous kernel of the stream (a search's emission, or whatever
+    // wrote the text) has finished before any global memory is touched
+    grid_dep_wait();
+    grid_dep_launch();
     __syncthreads();
 
     // phase 1: stream and filter (stages claimed dynamically)
@@ -677,6 +693,8 @@ __global__ void __launch_bounds__(stream::kEmitThreads, 4)
     using namespace stream;
     __shared__ StreamEmitSmem S;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    grid_dep_wait();  // the filter kernel's counts and masks are complete
+    grid_dep_launch();
     const uint32_t nr = P.nranges;
     const uint32_t per = (nr + kEmitThreads - 1) / kEmitThreads;
     const uint64_t *rt = reinterpret_cast<const uint64_t *>(P.range_total);
