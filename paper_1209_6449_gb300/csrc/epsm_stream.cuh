@@ -499,23 +499,57 @@ constexpr uint32_t kEmitDirect = 64;  // segments with at most this many hits sk
 __device__ __forceinline__ void emit_segment(uint64_t *positions, uint64_t capacity, uint32_t *err,
                                              int64_t s0, uint64_t idx0, uint2 packed,
                                              uint16_t *stage, int lane) {
-    uint64_t mk = ((uint64_t)packed.y << 32) | (uint64_t)packed.x;
-    const uint32_t c = (uint32_t)__popcll(mk);
+    uint32_t lo = packed.x, hi = packed.y;  // starts 64l .. 64l+31, 64l+32 .. 64l+63
+    const uint32_t c = (uint32_t)(__popc(lo) + __popc(hi));
     const uint32_t inc = warp_incl_scan(c, lane);
     const uint32_t total = __shfl_sync(kFull, inc, 31);
-    if (lane == 0 && idx0 + total > capacity) set_err(err, kErrCapacity);
+    // the whole segment fits in the output: no per-store bound check
+    const bool fits = idx0 + total <= capacity;
+    if (lane == 0 && !fits) set_err(err, kErrCapacity);
     const uint32_t pos0 = (uint32_t)lane * 64u;
-    uint32_t k = inc - c;  // the lane's next output index inside the segment
+    uint64_t *dst = positions + idx0;  // (unsigned arithmetic: s0 may be negative,
+    const uint64_t base = (uint64_t)s0; //  every emitted position is not)
+    uint32_t k = inc - c;  // the lane's first output index inside the segment
     if (total <= kEmitDirect) {
         // few hits: each lane writes its own (at most a few) positions
-        while (mk != 0ull) {
-            const uint32_t b = (uint32_t)(__ffsll((long long)mk) - 1);
-            mk &= mk - 1ull;
-            const uint64_t idx = idx0 + k++;
-            if (idx < capacity) positions[idx] = (uint64_t)(s0 + (int64_t)(pos0 + b));
+        while (lo) {
+            const uint32_t b = (uint32_t)(__ffs(lo) - 1);
+            lo &= lo - 1u;
+            if (fits || idx0 + k < capacity) dst[k] = base + pos0 + b;
+            ++k;
+        }
+        while (hi) {
+            const uint32_t b = (uint32_t)(__ffs(hi) - 1);
+            hi &= hi - 1u;
+            if (fits || idx0 + k < capacity) dst[k] = base + pos0 + 32u + b;
+            ++k;
         }
         return;
     }
+    if (total <= kEmitWindow) {
+        // the common dense case: one staging window
+        while (lo) {
+            const uint32_t b = (uint32_t)(__ffs(lo) - 1);
+            lo &= lo - 1u;
+            stage[k++] = (uint16_t)(pos0 + b);
+        }
+        while (hi) {
+            const uint32_t b = (uint32_t)(__ffs(hi) - 1);
+            hi &= hi - 1u;
+            stage[k++] = (uint16_t)(pos0 + 32u + b);
+        }
+        __syncwarp();
+        if (fits) {
+            for (uint32_t q = lane; q < total; q += 32u) dst[q] = base + stage[q];
+        } else {
+            for (uint32_t q = lane; q < total; q += 32u)
+                if (idx0 + q < capacity) dst[q] = base + stage[q];
+        }
+        __syncwarp();
+        return;
+    }
+    // very dense (more than one window): 64-bit mask, window by window
+    uint64_t mk = ((uint64_t)hi << 32) | (uint64_t)lo;
     for (uint32_t w0 = 0; w0 < total; w0 += kEmitWindow) {
         const uint32_t w1 = w0 + kEmitWindow;
         while (mk != 0ull && k < w1) {
@@ -528,7 +562,7 @@ __device__ __forceinline__ void emit_segment(uint64_t *positions, uint64_t capac
         const uint32_t nw = total - w0 < kEmitWindow ? total - w0 : kEmitWindow;
         for (uint32_t q = lane; q < nw; q += 32u) {
             const uint64_t idx = idx0 + w0 + q;
-            if (idx < capacity) positions[idx] = (uint64_t)(s0 + stage[q]);
+            if (idx < capacity) positions[idx] = base + stage[q];
         }
         __syncwarp();
     }
