@@ -1,5 +1,5 @@
 // Batched search with shared text passes: many (text, pattern) pairs in one
-// cooperative persistent launch, where all pairs on the same text form a group
+// persistent launch, where all pairs on the same text form a group
 // whose stages are loaded once and searched for every pattern of the group.
 //
 // Shared filter.  The patterns of a group with m >= 5 share one exact-match
