@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-pairs", type=int, default=8192)
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-rates", default="2000,10000,50000",
+    ap.add_argument("--serve-rates", default="2000,5000,10000,20000,50000",
                     help="Poisson arrival rates (queries/s) of the served workload")
     ap.add_argument("--serve-secs", type=float, default=1.0,
                     help="arrival window per rate for the serving engine")

@@ -122,6 +122,13 @@ epsm_status epsm_search_variant(epsm_ctx *ctx, int variant, const uint8_t *text,
  * more occurrences than its capacity, EPSM_ERR_CUDA on a CUDA error. */
 epsm_status epsm_sync(epsm_ctx *ctx, void *stream);
 
+/* Diagnostic of the bounded device waits: launches one warp that waits for a
+ * device flag nothing sets, giving up after limit_ns (1 ns .. 1 s) exactly as
+ * the search kernels' waits do.  The next epsm_sync returns EPSM_ERR_TIMEOUT
+ * and clears the condition; the context stays usable.  EPSM_ERR_ARG for a
+ * NULL context or a limit outside that range. */
+epsm_status epsm_wait_probe(epsm_ctx *ctx, uint64_t limit_ns, void *stream);
+
 /* Batched search over `npairs` independent (text, pattern) pairs of uneven n
  * and m, in one persistent launch (each pair is one Section 1 problem).
  *   texts      host array of npairs DEVICE text pointers

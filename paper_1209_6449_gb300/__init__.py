@@ -22,7 +22,7 @@ from ._native import (MAX_M, MAX_M_LONG, STATIC_MAX_TEXT, STATUS_NAMES, VARIANT_
 __all__ = ["Context", "EpsmError", "Server", "epsm_create", "epsm_destroy", "epsm_status_str",
            "epsm_search", "epsm_search_async", "epsm_search_variant", "epsm_sync",
            "epsm_search_batch", "epsm_search_host", "epsm_variant_for", "epsm_set_variant",
-           "epsm_launch_count", "epsm_search_static", "STATIC_MAX_TEXT", "MAX_M", "MAX_M_LONG", "VARIANT_AUTO", "VARIANT_DIRECT", "VARIANT_PREFIX4",
+           "epsm_launch_count", "epsm_search_static", "epsm_wait_probe", "STATIC_MAX_TEXT", "MAX_M", "MAX_M_LONG", "VARIANT_AUTO", "VARIANT_DIRECT", "VARIANT_PREFIX4",
            "VARIANT_PREFIX8", "VARIANT_BLOCK8", "VARIANT_BLOCK4", "VARIANT_CODE2", "VARIANT_ADAPT",
            "VARIANT_NAMES"]
 
@@ -86,6 +86,11 @@ def epsm_search_variant(ctx: int, variant: int, text: int, n: int, pattern: byte
 
 def epsm_sync(ctx: int, stream: int = 0) -> int:
     return _lib.epsm_sync(ctx, stream)
+
+
+def epsm_wait_probe(ctx: int, limit_ns: int, stream: int = 0) -> int:
+    """Diagnostic of the bounded device waits (see include/epsm.h)."""
+    return _lib.epsm_wait_probe(ctx, limit_ns, stream)
 
 
 def _pattern_table(patterns: Sequence[bytes]):

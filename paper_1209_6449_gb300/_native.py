@@ -62,6 +62,8 @@ def load(path: str | None = None):
     lib.epsm_search_variant.argtypes = [vp, i32, vp, u64, vp, u32, vp, u64, vp, vp]
     lib.epsm_search_variant.restype = st
     lib.epsm_sync.argtypes = [vp, vp]
+    lib.epsm_wait_probe.argtypes = [vp, u64, vp]
+    lib.epsm_wait_probe.restype = st
     lib.epsm_sync.restype = st
     lib.epsm_search_batch.argtypes = [vp, u32, vp, vp, vp, vp, vp, u64, vp, vp]
     lib.epsm_search_batch.restype = st

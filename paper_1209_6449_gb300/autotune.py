@@ -1,8 +1,9 @@
 """Autotuner for the per-m kernel variant (the EPSM dispatcher of Section 3
 chooses its procedure by m; on the GPU the choice is measured, not fixed).
 
-For every pattern length m it times each variant that covers m on texts of a
-few alphabet sizes (uniform random bytes over sigma symbols, with patterns
+For every pattern length m it times each variant that covers m on texts over
+the workloads' alphabets (uniform random bytes over the DNA letters ACGT, the
+20 amino-acid letters and a 64-symbol natural-language set, with patterns
 copied from the text) and keeps the variant with the smallest total time.  The
 table is written as JSON and installed into a context with ``apply``.
 ``Context`` loads ``tuning.json`` next to this file when it exists.
@@ -29,15 +30,20 @@ def variants_for(m: int):
     return [v for v, r in COVER.items() if m in r]
 
 
-def autotune(ctx, n: int = 64 << 20, sigmas=(4, 20, 64), ms=range(1, 33), reps: int = 3,
+ALPHABETS = (b"ACGT", b"ACDEFGHIKLMNPQRSTVWY",
+             b" abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ0123456789.")
+
+
+def autotune(ctx, n: int = 64 << 20, alphabets=ALPHABETS, ms=range(1, 33), reps: int = 3,
              patterns: int = 4, seed: int = 0) -> dict:
     """Measure every (m, variant) and return the tuning table."""
     import torch
     g = torch.Generator(device="cpu").manual_seed(seed)
     texts = []
-    for sigma in sigmas:
-        t = torch.randint(65, 65 + sigma, (n,), generator=g, dtype=torch.uint8)
-        texts.append(t.cuda())
+    for alpha in alphabets:
+        sym = torch.tensor(list(alpha), dtype=torch.uint8)
+        idx = torch.randint(0, len(alpha), (n,), generator=g)
+        texts.append(sym[idx].cuda())
     cap = n // 2
     out = torch.empty(cap, dtype=torch.int64, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
@@ -72,7 +78,7 @@ def autotune(ctx, n: int = 64 << 20, sigmas=(4, 20, 64), ms=range(1, 33), reps: 
     return {"variant": {str(m): v for m, v in table.items()},
             "names": {str(m): VARIANT_NAMES[v] for m, v in table.items()},
             "ms_per_search": {str(m): d for m, d in detail.items()},
-            "text_bytes": n, "sigmas": list(sigmas), "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+            "text_bytes": n, "alphabets": [a.decode() for a in alphabets], "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
 
 
 def apply(ctx, table: dict) -> None:

@@ -936,6 +936,37 @@ EPSM_API epsm_status epsm_search(epsm_ctx *c, const uint8_t *text, uint64_t n,
     return *count > capacity ? EPSM_ERR_CAPACITY : EPSM_OK;
 }
 
+// Diagnostic: one warp waits, bounded by limit_ns, for a device flag that
+// nothing sets, as every wait of the search kernels is bounded; when the
+// limit passes it sets the context's timeout bit, which the next epsm_sync
+// reports.  Shows that a wait that gives up leaves the context usable.
+__global__ void wait_probe_kernel(const uint32_t *flag, uint32_t *err, uint64_t limit_ns) {
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        uint32_t v;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v) return;
+        if (globaltimer_ns() - t0 > limit_ns) {
+            if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
+            return;
+        }
+        __nanosleep(1000);
+    }
+}
+
+EPSM_API epsm_status epsm_wait_probe(epsm_ctx *c, uint64_t limit_ns, void *stream) {
+    if (!c || limit_ns == 0 || limit_ns > 1000000000ull) return EPSM_ERR_ARG;
+    cudaStream_t s = pick_stream(c, stream);
+    epsm_status st = order_after_previous(c, s);
+    if (st != EPSM_OK) return st;
+    // the flag: a scratch word nothing sets
+    CK(cudaMemsetAsync(&c->misc->probe, 0, sizeof(uint32_t), s));
+    wait_probe_kernel<<<1, 32, 0, s>>>(&c->misc->probe, &c->misc->err, limit_ns);
+    CK(cudaGetLastError());
+    c->launches += 1;
+    return mark_done(c, s);
+}
+
 EPSM_API epsm_status epsm_sync(epsm_ctx *c, void *stream) {
     if (!c) return EPSM_ERR_ARG;
     uint32_t err = 0;

@@ -60,6 +60,7 @@ def test_status_strings_and_null_context():
     assert lib.epsm_search_async(None, None, 0, b"a", 1, None, 0, None, None) == 1
     assert lib.epsm_destroy(None) == 0
     assert lib.epsm_variant_for(None, 4) == 0
+    assert lib.epsm_wait_probe(None, 1000, None) == 1
 
 
 def test_server_arguments_checked_on_the_host():

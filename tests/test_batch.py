@@ -118,3 +118,21 @@ def test_batch_graph_replay_and_reuse(ctx, torch):
         for i, w in enumerate(want):
             assert np.array_equal(out[offs[i]:offs[i + 1]], w), (seed, i)
     print("batch graph replay:", ctx.batch_uses_graph)
+
+
+@pytest.mark.gpu
+def test_autotuner_small_run():
+    """The autotuner measures every variant that covers each m and returns a
+    table of variants that cover their m; the context accepts it."""
+    import paper_1209_6449_gb300 as epsm
+    from paper_1209_6449_gb300 import autotune
+    ctx = epsm.Context(0, tuning=None)
+    try:
+        res = autotune.autotune(ctx, n=1 << 20, ms=(2, 6, 9, 20), reps=1, patterns=1)
+        for m, v in res["variant"].items():
+            assert int(m) in autotune.COVER[v], (m, v)
+            assert set(res["ms_per_search"][m]) == {epsm.VARIANT_NAMES[x] for x in autotune.variants_for(int(m))}
+        autotune.apply(ctx, res)
+        assert all(ctx.variant_for(int(m)) == v for m, v in res["variant"].items())
+    finally:
+        ctx.close()

@@ -179,3 +179,16 @@ def test_generators_host_equals_device(torch):
             dev = torch.zeros(n, dtype=torch.uint8, device="cuda")
             spec.device(n, dev.data_ptr(), torch.cuda.current_stream().cuda_stream, start=start)
             assert np.array_equal(dev.cpu().numpy(), host), kind
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable(ctx, torch, epsm):
+    """A device wait on a flag that nothing sets gives up after its limit: the
+    next sync reports EPSM_ERR_TIMEOUT once, and searches work afterwards."""
+    s = torch.cuda.current_stream().cuda_stream
+    assert epsm.epsm_wait_probe(ctx.handle, 20_000_000, s) == 0
+    assert epsm.epsm_sync(ctx.handle, s) == 5   # EPSM_ERR_TIMEOUT
+    assert epsm.epsm_sync(ctx.handle, s) == 0   # reported once, then cleared
+    dev = torch.zeros(1000, dtype=torch.uint8, device="cuda")
+    assert ctx.count(dev, b"\x00\x00\x00") == 998
+    assert epsm.epsm_wait_probe(ctx.handle, 0, s) == 1        # EPSM_ERR_ARG
+    assert epsm.epsm_wait_probe(ctx.handle, 2 * 10**9, s) == 1
