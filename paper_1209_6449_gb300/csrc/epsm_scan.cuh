@@ -19,6 +19,14 @@
 
 namespace epsm {
 
+// Filter-soundness build (-DEPSM_FILTER_SOUNDNESS=1, a test build): the
+// single-search filters pass every start, so that the verification alone
+// decides; its results must equal those of the normal build.
+#ifndef EPSM_FILTER_SOUNDNESS
+#define EPSM_FILTER_SOUNDNESS 0
+#endif
+constexpr bool kSoundness = EPSM_FILTER_SOUNDNESS != 0;
+
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kFull = 0xffffffffu;

@@ -319,7 +319,8 @@ __device__ __forceinline__ uint32_t segment_hits(const SearchJob &J, const uint4
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const uint32_t z = ~(acc[u] | (acc[u] >> 1)) & 0x55555555u;
+            // (soundness build: every start is a candidate)
+            const uint32_t z = kSoundness ? 0x55555555u : ~(acc[u] | (acc[u] >> 1)) & 0x55555555u;
             uint32_t hh = 0u;
             if (__any_sync(kFull, z != 0u)) {
                 const uint4 nsrc = (lane == 0) ? (u + 1 < 4 ? ch[u + 1 < 4 ? u + 1 : u] : halo) : ch[u];

@@ -147,6 +147,7 @@ __device__ __forceinline__ uint32_t block_candidates(const SearchJob &J, const u
         if (t0 && cur.x == lo && cur.y == hi) cand |= 1u << (7 - j);
         if (t1 && cur.z == lo && cur.w == hi) cand |= 1u << (15 - j);
     }
+    if (kSoundness) cand = 0xFFFFu;  // soundness build: no block compare either
     uint32_t h = 0u;
     while (cand) {
         int i = __ffs(cand) - 1;
@@ -299,6 +300,13 @@ __device__ __forceinline__ uint32_t chunk_hits(const SearchJob &J, const uint4 c
 #pragma unroll
         for (int k = 0; k < 4; ++k) h |= nibble_of(z[k]) << (4 * k);
         return h;
+    } else if constexpr (kSoundness && (V == V_PREFIX4 || V == V_PREFIX8 || V == V_BLOCK4)) {
+        // soundness build: every start is a candidate, checked in full
+        const uint32_t n0 = __shfl_sync(kFull, nsrc.x, src);
+        const uint32_t n1 = __shfl_sync(kFull, nsrc.y, src);
+        const uint32_t n2 = __shfl_sync(kFull, nsrc.z, src);
+        const uint32_t n3 = __shfl_sync(kFull, nsrc.w, src);
+        return verify_cands_regs(pat, cur, n0, n1, n2, n3, 0xFFFFu);
     } else if constexpr (V == V_PREFIX4) {
         // Section 3.3 (EPSMb) with a 4-byte prefix: exact prefix test per start,
         // then the remaining bytes are checked in registers.
@@ -378,8 +386,8 @@ __device__ __forceinline__ uint32_t chunk_hits(const SearchJob &J, const uint4 c
         // which is then checked in full.
         const uint32_t h0 = block_hash(cur.x, cur.y);
         const uint32_t h1 = block_hash(cur.z, cur.w);
-        const uint32_t t0 = table[h0];
-        const uint32_t t1 = table[h1];
+        const uint32_t t0 = kSoundness ? 1u : table[h0];  // soundness build: every block marked
+        const uint32_t t1 = kSoundness ? 1u : table[h1];
         if (t0 | t1) return block_candidates(J, cur, p0, pblk, t0, t1, T);
         return 0u;
     }
