@@ -71,9 +71,12 @@ typedef enum {
                                   7 <= m <= 16 (Section 3.4's aligned-block idea with 4-byte blocks) */
     EPSM_VARIANT_CODE2 = 6,    /* 2-bit codes (bits 1..2 of every byte) of the first min(m, 8) bytes
                                   as the filter + verify, 2 <= m <= 16 (Section 3.3's filter-then-verify) */
-    EPSM_VARIANT_ADAPT = 7     /* 5 <= m <= 16: per warp and epoch of segments, the 2-bit code filter
-                                  where the text makes 4-byte block matches frequent (small alphabets),
-                                  else BLOCK4 (m >= 7) or PREFIX4 */
+    EPSM_VARIANT_ADAPT = 7,    /* 5 <= m <= 16: per block, the 2-bit code filter where the text makes
+                                  4-byte block matches frequent (small alphabets), else BLOCK4
+                                  (m >= 7) or PREFIX4 */
+    EPSM_VARIANT_BLOCK8S = 8   /* 23 <= m <= 32, single search: BLOCK8 with the block stride sh of
+                                  Section 3.4 (every second aligned block inspected, 16 pattern blocks
+                                  in the table); batched searches run it as BLOCK8 */
 } epsm_variant;
 
 /* Create a context on CUDA device `device`.  `flags` is reserved (pass 0).

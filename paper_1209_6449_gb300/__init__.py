@@ -16,14 +16,14 @@ import numpy as np
 
 from . import _native
 from ._native import (MAX_M, MAX_M_LONG, STATIC_MAX_TEXT, STATUS_NAMES, VARIANT_AUTO, VARIANT_BLOCK4, VARIANT_BLOCK8,
-                      VARIANT_ADAPT, VARIANT_CODE2, VARIANT_DIRECT, VARIANT_NAMES, VARIANT_PREFIX4,
-                      VARIANT_PREFIX8)
+                      VARIANT_ADAPT, VARIANT_BLOCK8S, VARIANT_CODE2, VARIANT_DIRECT, VARIANT_NAMES,
+                      VARIANT_PREFIX4, VARIANT_PREFIX8)
 
 __all__ = ["Context", "EpsmError", "Server", "epsm_create", "epsm_destroy", "epsm_status_str",
            "epsm_search", "epsm_search_async", "epsm_search_variant", "epsm_sync",
            "epsm_search_batch", "epsm_search_host", "epsm_variant_for", "epsm_set_variant",
            "epsm_launch_count", "epsm_search_static", "epsm_wait_probe", "STATIC_MAX_TEXT", "MAX_M", "MAX_M_LONG", "VARIANT_AUTO", "VARIANT_DIRECT", "VARIANT_PREFIX4",
-           "VARIANT_PREFIX8", "VARIANT_BLOCK8", "VARIANT_BLOCK4", "VARIANT_CODE2", "VARIANT_ADAPT",
+           "VARIANT_PREFIX8", "VARIANT_BLOCK8", "VARIANT_BLOCK4", "VARIANT_CODE2", "VARIANT_ADAPT", "VARIANT_BLOCK8S",
            "VARIANT_NAMES"]
 
 _lib = _native.load()

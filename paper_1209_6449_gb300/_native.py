@@ -15,8 +15,8 @@ OK, ERR_ARG, ERR_CAPACITY, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT = range(6)
 STATUS_NAMES = ["EPSM_OK", "EPSM_ERR_ARG", "EPSM_ERR_CAPACITY", "EPSM_ERR_CUDA",
                 "EPSM_ERR_NOMEM", "EPSM_ERR_TIMEOUT"]
 (VARIANT_AUTO, VARIANT_DIRECT, VARIANT_PREFIX4, VARIANT_PREFIX8, VARIANT_BLOCK8, VARIANT_BLOCK4, VARIANT_CODE2,
- VARIANT_ADAPT) = range(8)
-VARIANT_NAMES = {1: "direct", 2: "prefix4", 3: "prefix8", 4: "block8", 5: "block4", 6: "code2", 7: "adapt"}
+ VARIANT_ADAPT, VARIANT_BLOCK8S) = range(9)
+VARIANT_NAMES = {1: "direct", 2: "prefix4", 3: "prefix8", 4: "block8", 5: "block4", 6: "code2", 7: "adapt", 8: "block8s"}
 MAX_M = 32
 MAX_M_LONG = 4096  # single-search entry points only
 

@@ -17,12 +17,12 @@ import os
 import sys
 import time
 
-from ._native import (VARIANT_ADAPT, VARIANT_BLOCK4, VARIANT_BLOCK8, VARIANT_CODE2, VARIANT_DIRECT,
-                      VARIANT_NAMES, VARIANT_PREFIX4, VARIANT_PREFIX8)
+from ._native import (VARIANT_ADAPT, VARIANT_BLOCK4, VARIANT_BLOCK8, VARIANT_BLOCK8S, VARIANT_CODE2,
+                      VARIANT_DIRECT, VARIANT_NAMES, VARIANT_PREFIX4, VARIANT_PREFIX8)
 
 COVER = {VARIANT_DIRECT: range(1, 5), VARIANT_PREFIX4: range(4, 16),
          VARIANT_PREFIX8: range(8, 16), VARIANT_BLOCK8: range(15, 33), VARIANT_BLOCK4: range(7, 17),
-         VARIANT_CODE2: range(2, 17), VARIANT_ADAPT: range(5, 17)}
+         VARIANT_CODE2: range(2, 17), VARIANT_ADAPT: range(5, 17), VARIANT_BLOCK8S: range(23, 33)}
 DEFAULT_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
 
 

@@ -46,11 +46,12 @@ bool variant_covers(int v, uint32_t m) {
         case V_BLOCK4: return m >= 7 && m <= 16;
         case V_CODE2: return m >= 2 && m <= 16;
         case V_ADAPT: return m >= 5 && m <= 16;
+        case V_BLOCK8S: return m >= 23 && m <= 32;
         default: return false;
     }
 }
 
-int variant_offset(int v) { return v == V_BLOCK8 ? -7 : 0; }
+int variant_offset(int v) { return v == V_BLOCK8 ? -7 : v == V_BLOCK8S ? -15 : 0; }
 
 Pattern pack_pattern(const uint8_t *p, uint32_t m) {
     Pattern pat;
@@ -290,6 +291,7 @@ cudaError_t launch_stream(int sms, int v, uint32_t m, stream::StreamParams &p,
         case V_BLOCK4: return launch_stream_t<V_BLOCK4, 4>(sms, p, s);
         case V_CODE2: return launch_stream_t<V_CODE2, 4>(sms, p, s);
         case V_ADAPT: return launch_stream_t<V_ADAPT, 4>(sms, p, s);
+        case V_BLOCK8S: return launch_stream_t<V_BLOCK8S, 8>(sms, p, s);
         default: return launch_stream_t<V_BLOCK8, 8>(sms, p, s);
     }
 }
@@ -670,7 +672,10 @@ epsm_status batch_submit(epsm_ctx *c, uint32_t npairs, const uint8_t *const *tex
         D.job = make_job(texts[i], ns[i], pack_pattern(patterns[i], m));
         // shared patterns are numbered like the window variants (offset 0);
         // short patterns of a shared text run the direct compare
-        D.variant = (uint32_t)(kstr[i] ? V_PREFIX4 : multi[i] ? V_DIRECT : c->variant[m]);
+        // (the strided block variant is single-search only: its batch form is
+        // the plain block variant)
+        const int vt = c->variant[m] == V_BLOCK8S ? V_BLOCK8 : c->variant[m];
+        D.variant = (uint32_t)(kstr[i] ? V_PREFIX4 : multi[i] ? V_DIRECT : vt);
         const uint64_t nst = stages_for(D.job.delta, ns[i], m, (int)D.variant);
         if (nst == 0) continue;
         D.pair = i;

@@ -39,6 +39,7 @@ constexpr int V_BLOCK8 = 4;
 constexpr int V_BLOCK4 = 5;
 constexpr int V_CODE2 = 6;
 constexpr int V_ADAPT = 7;
+constexpr int V_BLOCK8S = 8;
 
 // Block fingerprint table (Section 3.4): k = 11 bits -> 2048 one-byte slots.
 constexpr int kHashBits = 11;

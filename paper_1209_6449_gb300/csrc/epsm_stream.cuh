@@ -56,7 +56,7 @@ struct alignas(128) StreamSmem {
     uint32_t votes;              // adaptive variant: consumer warps whose probe found dense text
     uint64_t full[kStages];
     uint64_t empty[kStages];
-    uint32_t pblk[16];
+    uint32_t pblk[32];
     uint8_t table[kHashSlots];
 };
 
@@ -373,10 +373,10 @@ __device__ __forceinline__ uint32_t stage_hits(const SearchJob &J, uint64_t cf0,
                                                uint64_t c0, int w, int lane, uint32_t (&h)[4],
                                                bool *dense_out = nullptr, const uint8_t *tail = nullptr,
                                                uint32_t mtail = 0u) {
-    constexpr int OFF = (V == V_BLOCK8) ? -7 : 0;
+    constexpr int OFF = (V == V_BLOCK8) ? -7 : (V == V_BLOCK8S) ? -15 : 0;
     uint4 ch[4];
     uint4 halo;
-    load_segment(J, cf0, cf1, buf, c0, w, lane, V != V_BLOCK8, ch, halo);
+    load_segment(J, cf0, cf1, buf, c0, w, lane, V != V_BLOCK8 && V != V_BLOCK8S, ch, halo);
     StagedText T;
     T.buf = buf;
     T.sbase = (int64_t)(c0 * 16u);
@@ -700,6 +700,7 @@ __global__ void __launch_bounds__(stream::kThreadsStream, stream::kMaxBlocksPerS
     }
     // S1: pattern preprocessing (block fingerprint table, Section 3.4)
     if (V == V_BLOCK8) build_block_table(P.job.pat, S.table, S.pblk);
+    if (V == V_BLOCK8S) build_block_table16(P.job.pat, S.table, S.pblk);
     // the previous kernel of the stream (a search's emission, or whatever
     // wrote the text) has finished before any global memory is touched
     grid_dep_wait();

@@ -35,6 +35,28 @@ __device__ __forceinline__ void build_block_table(const Pattern &pat, uint8_t *t
     __syncthreads();
 }
 
+// The table of the strided block variant (Section 3.4 with the stride
+// sh of two blocks, 23 <= m <= 32): only every second aligned block is
+// inspected, so an occurrence's first inspected block lies at j = 0..15 and
+// the table holds the sixteen blocks p[j..j+7], j < 16 (pblk: 32 words).
+__device__ __forceinline__ void build_block_table16(const Pattern &pat, uint8_t *table,
+                                                    uint32_t *pblk) {
+    uint32_t *tw = reinterpret_cast<uint32_t *>(table);
+    for (int i = threadIdx.x; i < kHashSlots / 4; i += blockDim.x) tw[i] = 0u;
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        const int j = threadIdx.x;
+        const int q = j >> 2;
+        const uint32_t sh = 8u * (uint32_t)(j & 3);
+        const uint32_t lo = __funnelshift_r(pat.w[q], pat.w[q + 1], sh);
+        const uint32_t hi = __funnelshift_r(pat.w[q + 1], pat.w[q + 2], sh);
+        pblk[2 * j] = lo;
+        pblk[2 * j + 1] = hi;
+        table[block_hash(lo, hi)] = 1;
+    }
+    __syncthreads();
+}
+
 // Broadcast words (p_j)^4 of the first eight pattern bytes (Section 3.2, table B).
 struct BcastWords {
     uint32_t b[8];
@@ -223,6 +245,26 @@ __device__ __forceinline__ uint32_t even_bits(uint32_t z) {
     return (z | (z >> 8)) & 0x0000FFFFu;
 }
 
+// Strided block variant, slow path: the chunk's first block hit a marked slot;
+// a match with p[j..j+7] (j < 16) gives the candidate 16c - j, bit 15 - j of
+// the chunk's starts 16c - 15 .. 16c, checked in full.
+__device__ __forceinline__ uint32_t block16_candidates(const SearchJob &J, const uint4 cur, int64_t p0,
+                                                       const uint32_t *pblk, const StagedText &T) {
+    uint32_t cand = 0u;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+        if (cur.x == pblk[2 * j] && cur.y == pblk[2 * j + 1]) cand |= 1u << (15 - j);
+    if (kSoundness) cand = 0xFFFFu;
+    uint32_t h = 0u;
+    while (cand) {
+        const int i = __ffs(cand) - 1;
+        cand &= cand - 1u;
+        const int64_t P = p0 + i;
+        if (P >= (int64_t)J.delta && P <= J.pmax && verify_staged(J, P, T)) h |= 1u << i;
+    }
+    return h;
+}
+
 // 4-byte block variant, slow path: a word k of the chunk (k = 0..3) or the
 // next chunk's first word (k = 4) equals a pattern block p[j..j+3] (q[j]); the
 // match gives the candidate start 4k - j when it lies in the chunk
@@ -379,6 +421,13 @@ __device__ __forceinline__ uint32_t chunk_hits(const SearchJob &J, const uint4 c
             if (any) h = block4_candidates(pat, cur, n0, n1, n2, n3, q0, q1, q2, q3);
         }
         return h;
+    } else if constexpr (V == V_BLOCK8S) {
+        // Section 3.4 (EPSMc) with the block stride sh of two blocks: only
+        // the chunk's first block is fingerprinted (half the hashing and
+        // lookups of the plain block variant); starts 16c - 15 .. 16c.
+        const uint32_t t0 = kSoundness ? 1u : table[block_hash(cur.x, cur.y)];
+        if (t0) return block16_candidates(J, cur, p0, pblk, T);
+        return 0u;
     } else {
         // Section 3.4 (EPSMc) on aligned 8-byte blocks: fingerprint each block,
         // and where the slot is marked compare the block with the pattern

@@ -39,6 +39,7 @@ VARIANTS = {  # variant -> covered m
     5: range(7, 17),
     6: range(2, 17),
     7: range(5, 17),
+    8: range(23, 33),
 }
 
 

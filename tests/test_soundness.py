@@ -14,7 +14,7 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 VARIANTS = {2: range(4, 16), 3: range(8, 16), 4: range(15, 33), 5: range(7, 17),
-            6: range(2, 17), 7: range(5, 17)}
+            6: range(2, 17), 7: range(5, 17), 8: range(23, 33)}
 
 
 @pytest.fixture(scope="module")
