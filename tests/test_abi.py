@@ -96,3 +96,22 @@ def test_package_does_not_reach_the_oracle():
             "assert 'oracle' not in sys.modules; print('clean')" % ROOT)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
     assert out.returncode == 0 and "clean" in out.stdout, out.stderr
+
+
+def test_shipped_tuning_table_is_consistent():
+    """tuning.json (written by the autotuner on a GPU) names, for every m in
+    1..32, a variant that covers m; the names match the variant numbers."""
+    import json
+    path = os.path.join(ROOT, "paper_1209_6449_gb300", "tuning.json")
+    if not os.path.exists(path):
+        pytest.skip("no tuning table shipped")
+    with open(path) as f:
+        tab = json.load(f)
+    cover = {1: range(1, 5), 2: range(4, 16), 3: range(8, 16), 4: range(15, 33), 5: range(7, 17),
+             6: range(2, 17), 7: range(5, 17), 8: range(23, 33)}
+    names = {1: "direct", 2: "prefix4", 3: "prefix8", 4: "block8", 5: "block4", 6: "code2",
+             7: "adapt", 8: "block8s"}
+    assert sorted(int(m) for m in tab["variant"]) == list(range(1, 33))
+    for m, v in tab["variant"].items():
+        assert int(m) in cover[v], (m, v)
+        assert tab["names"][m] == names[v]
