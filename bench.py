@@ -1,18 +1,28 @@
 #!/usr/bin/env python3
 """Benchmark: exact short-pattern search throughput on GB300.
 
-Workload (default ``sweep``, the pattern-length sweep): three synthetic texts of
-n = 256 MiB each — sigma=4 uniform DNA-like, sigma=20 uniform protein-like,
-sigma=64 natural-language-like (Zipf s=1.1 with a 15% space symbol) — and for
-each text 100 patterns per m in {2, 4, 8, 16, 32}, half copied from random text
-offsets and half drawn i.i.d. from the text's symbol distribution.  One step
-searches every (text, pattern) pair: 1500 searches, 402.7 GB of text.  Each
-search produces its count and all sorted uint64 start positions.
+Workload (default, the large single-GPU scan): three synthetic texts of
+n = 16 GiB each, resident in HBM -- sigma=4 uniform DNA-like bytes, an order-2
+Markov chain over 96 printable ASCII bytes with seeded transition rows, and
+the DNA-like text with seeded runs of ``A`` covering about 5% of its bytes.
+For the DNA-like and Markov texts, m in {2,3,4,6,8,12,16,24,32} with one
+pattern copied from a random text offset and one drawn i.i.d. from the text's
+symbol distribution; for the runs text the adversarial periodic pattern A^m
+for every m.  One step searches every (text, pattern) pair: 45 searches,
+773 GB of text.  Each search produces its count and all sorted uint64 start
+positions.
 
 Metric: text GB/s (bytes of text scanned / second), device-timed with the
-texts resident in HBM.  ``e2e`` is the same metric through the public C entry
-point that takes HOST buffers (epsm_search_host), with the texts' host->device
-copies and the positions' device->host copies inside the timed region.
+texts resident in HBM (inputs far larger than the 129 MB L2).  ``per_text_m``
+breaks it down per (text, m) from a separate pass with CUDA events between
+searches, with the fraction of the measured HBM peak taken on the algorithmic
+bytes (n + 8 per position + 8).  ``e2e`` is the same metric through the public
+C entry point that takes HOST buffers (epsm_search_host: one call per text,
+its single searches, the text's host->device copy and the positions'
+device->host copy inside the timed region).  ``sweep`` is the pattern-length
+sweep (three 256 MiB texts, m in {2,4,8,16,32}, 100 patterns each);
+``batched`` and ``served`` are the batched and served workloads against the
+plain per-pair / per-query launch path.
 
 ``--impl reference`` times the CPU oracle (brute-force scan) on the host cores
 on a bounded sample of the same workload.
@@ -36,13 +46,19 @@ import numpy as np  # noqa: E402
 
 GiB = 1 << 30
 MiB = 1 << 20
-METRIC = "text GB/s (pattern-length sweep, m=2..32)"
 UNIT = "GB/s"
+L2_BYTES = 129 * 10**6
+# large single-GPU scan (the headline)
+METRIC = "text GB/s (large single-GPU scan, m=2..32, 16 GiB texts)"
+SCAN_KINDS = ("dna", "markov96", "dna_runs")
+SCAN_MS = (2, 3, 4, 6, 8, 12, 16, 24, 32)
+SCAN_N = 16 * GiB
+# pattern-length sweep
+SWEEP_METRIC = "text GB/s (pattern-length sweep, m=2..32, 256 MiB texts)"
 KINDS = ("dna", "protein", "nl64")
 MS = (2, 4, 8, 16, 32)
 PATS_PER_M = 100
 TEXT_N = 256 * MiB
-L2_BYTES = 129 * 10**6
 
 
 def parse():
@@ -51,18 +67,22 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="epsm", choices=["epsm", "reference"])
+    ap.add_argument("--workload", default="scan", choices=["scan", "sweep"],
+                    help="headline workload: the large single-GPU scan (default) or the "
+                         "pattern-length sweep")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the sweep's extra key")
     ap.add_argument("--patterns", type=int, default=PATS_PER_M,
-                    help="patterns per (text, m); the workload uses 100")
+                    help="sweep: patterns per (text, m); the workload uses 100")
     ap.add_argument("--case", default=None,
-                    help="KIND:M[:VARIANT[:N[:count]]] — time one search of an N-byte text "
-                         "(default 256 MiB; 'count': count only) and exit (the small case "
-                         "used for ncu captures)")
+                    help="KIND:M[:VARIANT[:N[:MODE]]] -- time one search of an N-byte text "
+                         "(default 256 MiB) and exit (the small cases of ncu captures); MODE "
+                         "'count': count only; 'iid': an i.i.d. pattern instead of a planted "
+                         "one; 'runs': the pattern A^m")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--sample", action="store_true",
-                    help="one search per (text, m) of the sweep (15 launches) and exit; the "
-                         "launches an ncu traffic capture measures")
+                    help="one search per (text, m) of the sweep (15 launches) and exit")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-pairs", type=int, default=8192)
     ap.add_argument("--no-serve", action="store_true")
@@ -82,14 +102,20 @@ def run_case(args):
     import paper_1209_6449_gb300 as epsm
     parts = args.case.split(":")
     kind, m = parts[0], int(parts[1])
-    variant = int(parts[2]) if len(parts) > 2 else 0
-    n = int(parts[3]) if len(parts) > 3 else TEXT_N
-    count_only = len(parts) > 4 and parts[4] == "count"
+    variant = int(parts[2]) if len(parts) > 2 and parts[2] else 0
+    n = int(parts[3]) if len(parts) > 3 and parts[3] else TEXT_N
+    mode = parts[4] if len(parts) > 4 else ""
     ctx = epsm.Context(0)
+    spec = gen.TextSpec(kind, 0)
     t = torch.empty(n, dtype=torch.uint8, device="cuda")
-    gen.TextSpec(kind, 0).device(n, t.data_ptr(), torch.cuda.current_stream().cuda_stream)
-    pat = gen.planted_patterns(gen.TextSpec(kind, 0), n, m, 1)[0]
-    cap = 0 if count_only else n // 3
+    spec.device(n, t.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    if mode == "runs":
+        pat = b"A" * m
+    elif mode == "iid":
+        pat = gen.random_patterns(spec, m, 1)[0]
+    else:
+        pat = gen.planted_patterns(spec, n, m, 1)[0]
+    cap = 0 if mode == "count" else n // 3
     out = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     times = []
@@ -102,25 +128,57 @@ def run_case(args):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     st = ctx.sync()
-    print(json.dumps({"case": args.case, "n": n, "count": int(cnt.item()), "status": st,
+    c = int(cnt.item())
+    best = min(times)
+    print(json.dumps({"case": args.case, "n": n, "count": c, "status": st,
                       "ms": [round(x, 4) for x in times],
-                      "gbs_best": round(n / min(times) / 1e6, 1)}), flush=True)
+                      "gbs_best": round(n / best / 1e6, 1),
+                      "alg_gbs_best": round((n + 8 * c + 8) / best / 1e6, 1)}), flush=True)
     ctx.close()
     return 0 if st == 0 else 1
 
 
-def workload_patterns(npat):
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def scan_patterns():
+    """(text, m, kind of pattern, pattern) of one step of the large scan."""
+    import gen
+    out = []
+    for kind in ("dna", "markov96"):
+        spec = gen.TextSpec(kind, 0)
+        for m in SCAN_MS:
+            out.append((kind, m, "planted", gen.planted_patterns(spec, SCAN_N, m, 1)[0]))
+            out.append((kind, m, "iid", gen.random_patterns(spec, m, 1)[0]))
+    for m in SCAN_MS:
+        out.append(("dna_runs", m, "runs", b"A" * m))
+    return out
+
+
+def scan_config(ngpus):
+    return {"workload": "large single-GPU scan: 16 GiB sigma-4 uniform DNA-like text, 16 GiB "
+                        "order-2 Markov text over 96 printable bytes, 16 GiB DNA-like text with "
+                        "5% runs of A; m in {2,3,4,6,8,12,16,24,32}: one planted and one i.i.d. "
+                        "pattern per (text, m) on the first two, A^m on the runs text",
+            "text_bytes": SCAN_N, "texts": list(SCAN_KINDS), "m": list(SCAN_MS),
+            "searches_per_step": 2 * 2 * len(SCAN_MS) + len(SCAN_MS),
+            "l2": "inputs larger than L2 (16 GiB texts vs 129 MB L2); no flush",
+            "parallelism": f"replicas x{ngpus}" if ngpus > 1 else "single GPU"}
+
+
+def sweep_patterns(npat):
     import gen
     out = []
     for kind in KINDS:
         spec = gen.TextSpec(kind, 0)
         for m in MS:
-            for p in gen.mixed_patterns(spec, TEXT_N, m, npat):
-                out.append((kind, m, p))
+            for i, p in enumerate(gen.mixed_patterns(spec, TEXT_N, m, npat)):
+                out.append((kind, m, "planted" if i < npat - npat // 2 else "iid", p))
     return out
 
 
-def config(npat, ngpus):
+def sweep_config(npat, ngpus):
     return {"workload": "pattern-length sweep: 3 texts x 256 MiB (sigma 4 DNA-like, sigma 20 "
                         "protein-like, sigma 64 Zipf natural-language-like), m in {2,4,8,16,32}, "
                         f"{npat} patterns per (text, m), half planted half i.i.d.",
@@ -193,55 +251,67 @@ class ClockSampler:
 # reference arm / CPU baseline: the oracle on the host cores
 # ---------------------------------------------------------------------------
 
-def oracle_sample(budget_s, texts_host):
-    """Time the oracle on a bounded sample: the first 8 MiB of each text, two
-    patterns per (text, m), repeated until about budget_s seconds."""
+def oracle_jobs(workload, sample_n):
+    """A bounded sample of the workload for the oracle: the first sample_n
+    bytes of each text, one pattern per (text, m)."""
     import gen
+    if workload == "scan":
+        texts = {k: gen.TextSpec(k, 0).host_parallel(sample_n) for k in SCAN_KINDS}
+        pats = [(k, m, p) for (k, m, kind, p) in scan_patterns() if kind != "iid"]
+        desc = "3 texts x 9 m x 1 pattern (planted; A^m on the runs text)"
+    else:
+        texts = {k: gen.TextSpec(k, 0).host(sample_n) for k in KINDS}
+        pats = [(k, m, gen.mixed_patterns(gen.TextSpec(k, 0), TEXT_N, m, 2)[0])
+                for k in KINDS for m in MS]
+        desc = "3 texts x 5 m x 1 pattern (planted)"
+    return [(texts[k], p) for (k, m, p) in pats], desc
+
+
+def oracle_rate(jobs, threads, budget_s):
+    """Rounds of the oracle over the jobs until about budget_s seconds."""
     import oracle
-    cores = os.cpu_count() or 1
-    sample_n = 8 * MiB
-    jobs = []
-    for kind in KINDS:
-        spec = gen.TextSpec(kind, 0)
-        t = texts_host[kind][:sample_n] if texts_host else spec.host(sample_n)
-        for m in MS:
-            for p in gen.mixed_patterns(spec, TEXT_N, m, 2):
-                jobs.append((t, p))
-    scanned, t0 = 0, time.perf_counter()
-    rounds = 0
+    scanned, rounds = 0, 0
+    t0 = time.perf_counter()
     while True:
         for t, p in jobs:
-            oracle.count(t, p, threads=cores)
+            oracle.search(t, p, threads=threads)
             scanned += t.size
         rounds += 1
         if time.perf_counter() - t0 >= budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": round(scanned / dt / 1e9, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{rounds} round(s) of {len(jobs)} searches (3 texts x 5 m x 2 patterns) "
-                      f"over the first 8 MiB of each text, brute-force C oracle on {cores} threads"}
+    return scanned / dt / 1e9, rounds
+
+
+def cpu_baseline(workload, budget_s=10.0):
+    """The oracle (count and all positions) timed on all host cores and on one
+    core, on a bounded sample of the workload."""
+    cores = os.cpu_count() or 1
+    sample_n = 16 * MiB if workload == "scan" else 8 * MiB
+    jobs, desc = oracle_jobs(workload, sample_n)
+    v_all, r_all = oracle_rate(jobs, cores, budget_s)
+    v_one, r_one = oracle_rate(jobs, 1, budget_s)
+    sample = (f"{len(jobs)} searches ({desc}) over the first {sample_n // MiB} MiB of each text, "
+              f"brute-force C oracle returning all positions")
+    return {"value": round(v_all, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{r_all} round(s) of {sample} on {cores} threads",
+            "single_thread": {"value": round(v_one, 4), "unit": UNIT, "cores": 1,
+                              "sample": f"{r_one} round(s) of {sample} on 1 thread"}}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    import gen
     import oracle
     cores = os.cpu_count() or 1
-    sample_n = 4 * MiB
-    jobs = []
-    for kind in KINDS:
-        spec = gen.TextSpec(kind, 0)
-        t = spec.host(sample_n)
-        for m in MS:
-            p = gen.mixed_patterns(spec, TEXT_N, m, 2)[0]
-            jobs.append((t, p))
+    sample_n = 8 * MiB if args.workload == "scan" else 4 * MiB
+    jobs, desc = oracle_jobs(args.workload, sample_n)
 
     def step():
         tot = 0
         for t, p in jobs:
-            oracle.count(t, p, threads=cores)
+            oracle.search(t, p, threads=cores)
             tot += t.size
         return tot
 
@@ -253,13 +323,15 @@ def run_reference(args):
         tot += step()
     dt = time.perf_counter() - t0
     v = tot / dt / 1e9
-    sample = (f"each step: 15 searches (3 texts x 5 m x 1 pattern) over the first 4 MiB of each "
-              f"text, brute-force C oracle on {cores} threads")
-    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT,
+    sample = (f"each step: {len(jobs)} searches ({desc}) over the first {sample_n // MiB} MiB of "
+              f"each text, brute-force C oracle returning all positions, on {cores} threads")
+    cfg = scan_config(args.gpus) if args.workload == "scan" else sweep_config(args.patterns, args.gpus)
+    line = {"impl": "reference", "metric": METRIC if args.workload == "scan" else SWEEP_METRIC,
+            "value": round(v, 4), "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": config(args.patterns, args.gpus),
+            "config": cfg,
             "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -290,10 +362,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources; else None."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+def profiled_traffic(workload):
+    """DRAM bytes per search from the committed ncu summary of this workload,
+    if it was taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
@@ -308,8 +380,7 @@ def profiled_traffic():
 # ---------------------------------------------------------------------------
 
 def run_sample(args):
-    """One search per (text, m) of the sweep, with the first (planted) pattern:
-    the launches the committed DRAM-traffic capture covers."""
+    """One search per (text, m) of the sweep, with the first (planted) pattern."""
     import torch
     import gen
     import paper_1209_6449_gb300 as epsm
@@ -334,6 +405,186 @@ def run_sample(args):
                       "status": st}), flush=True)
     ctx.close()
     return 0 if st == 0 else 1
+
+
+def make_texts(torch, dev, kinds, n, stream):
+    import gen
+    texts = {}
+    for kind in kinds:
+        t = torch.empty(n, dtype=torch.uint8, device=dev)
+        gen.TextSpec(kind, 0).device(n, t.data_ptr(), stream.cuda_stream)
+        texts[kind] = t
+    return texts
+
+
+def measure(ctx, torch, texts, pats, steps, warmup, stream, dist=None, clocks_index=None):
+    """Times `steps` passes over all (text, pattern) searches (after `warmup`
+    untimed passes): device time with CUDA events on the launching stream,
+    max over ranks.  Then one more pass with an event between searches gives
+    the per-search times.  Returns a dict of the measurements."""
+    n_by = {k: t.numel() for k, t in texts.items()}
+    nsearch = len(pats)
+    counts = torch.zeros(nsearch, dtype=torch.int64, device=stream.device)
+    # output room: the densest search of the workload (from a count-only pass)
+    for i, (kind, m, _, p) in enumerate(pats):
+        ctx.search_async(texts[kind], p, counts, 0, counts[i:i + 1], stream=stream)
+    torch.cuda.synchronize()
+    if ctx.sync() != 0:
+        raise SystemExit("device status after the count pass")
+    occ = counts.cpu().numpy().copy()
+    cap = int(occ.max()) + 1024
+    out = torch.empty(cap, dtype=torch.int64, device=stream.device)
+
+    def step():
+        for i, (kind, m, _, p) in enumerate(pats):
+            ctx.search_async(texts[kind], p, out, cap, counts[i:i + 1], stream=stream)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    if ctx.sync() != 0:
+        raise SystemExit("device status after warm-up")
+    if not np.array_equal(counts.cpu().numpy(), occ):
+        raise SystemExit("counts differ between the count pass and the searches")
+
+    clocks = ClockSampler(clocks_index if clocks_index is not None else 0)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches_before = ctx.launch_count
+    t_wall0 = time.time()
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if dist:
+        dist.barrier()
+    launches = ctx.launch_count - launches_before
+    elapsed_ms = e0.elapsed_time(e1)
+    clocks.stop()
+    if ctx.sync() != 0:
+        raise SystemExit("device status after the timed region")
+    if dist:
+        tt = torch.tensor([elapsed_ms], dtype=torch.float64, device=stream.device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+    # per-search times: one more pass with an event after every search
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(nsearch + 1)]
+    evs[0].record(stream)
+    for i, (kind, m, _, p) in enumerate(pats):
+        ctx.search_async(texts[kind], p, out, cap, counts[i:i + 1], stream=stream)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(nsearch)]
+    del out
+    text_bytes = sum(n_by[k] for (k, _, _, _) in pats)
+    alg_bytes = text_bytes + 8 * int(occ.sum()) + 8 * nsearch
+    return {"elapsed_ms": elapsed_ms, "steps": steps, "launches": launches, "occ": occ,
+            "per_search_ms": per, "text_bytes_per_step": text_bytes,
+            "alg_bytes_per_step": alg_bytes, "clocks": clocks.summary(t_wall0, t_wall1),
+            "n_by": n_by}
+
+
+def breakdown(pats, res, peak):
+    """Per (text, m, pattern kind): text GB/s and algorithmic GB/s of the
+    per-search pass (summed over that group's patterns), and the fraction of
+    the HBM peak on the algorithmic bytes."""
+    acc = {}
+    for i, (kind, m, pk, p) in enumerate(pats):
+        a = acc.setdefault((kind, m, pk), [0.0, 0, 0, 0])
+        n = res["n_by"][kind]
+        occ = int(res["occ"][i])
+        a[0] += res["per_search_ms"][i]
+        a[1] += occ
+        a[2] += n
+        a[3] += n + 8 * occ + 8
+    rows = {}
+    for (kind, m, pk), (ms, occ, nb, alg) in acc.items():
+        rows.setdefault(kind, {})[f"{m}/{pk}"] = {
+            "ms": round(ms, 3), "occ": occ, "text_gbs": round(nb / ms / 1e6, 1),
+            "alg_gbs": round(alg / ms / 1e6, 1), "frac": round(alg / ms / 1e6 / peak, 3)}
+    return rows
+
+
+def _mem_available():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def run_e2e(ctx, torch, texts, pats, steps, warmup, occ, dist=None):
+    """The same workload through epsm_search_host (host text in, host positions
+    out): every step copies each text from pinned host memory to the device,
+    runs its single searches and copies all positions back.  One call per text
+    with all its patterns when the pinned buffers fit in a third of the host's
+    available memory; otherwise a text's patterns are split over several calls
+    (each uploads the text again, counted in h2d_bytes_per_step)."""
+    from paper_1209_6449_gb300 import epsm_search_host
+    kinds = list(dict.fromkeys(k for (k, _, _, _) in pats))
+    text_bytes = sum(texts[k].numel() for k in kinds)
+    budget = max(_mem_available() // 3 - text_bytes, 1 << 30)
+    cap = max(int(occ.max()) + 1024, min(budget // 8, int(occ.sum()) + 1024))
+    calls = []  # (text kind, patterns)
+    for k in kinds:
+        cur, tot = [], 0
+        for i, (kk, _, _, p) in enumerate(pats):
+            if kk != k:
+                continue
+            if cur and tot + int(occ[i]) > cap - 1024:
+                calls.append((k, cur))
+                cur, tot = [], 0
+            cur.append(p)
+            tot += int(occ[i])
+        calls.append((k, cur))
+    hosts = {}
+    for k in kinds:
+        h = torch.empty(texts[k].numel(), dtype=torch.uint8, pin_memory=True)
+        h.copy_(texts[k])
+        hosts[k] = h.numpy()
+    pos_host = torch.empty(cap, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+
+    def step():
+        d2h = 0
+        for k, group in calls:
+            st, offs = epsm_search_host(ctx.handle, hosts[k], group, pos_host)
+            if st != 0:
+                raise SystemExit(f"epsm_search_host status {st}")
+            d2h += int(offs[-1]) * 8
+        return d2h
+
+    for _ in range(warmup):
+        step()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(steps):
+        d2h = step()
+    dt = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([dt], dtype=torch.float64, device=texts[kinds[0]].device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dt = float(tt.item())
+    world = dist.get_world_size() if dist else 1
+    scanned = sum(texts[k].numel() for (k, _, _, _) in pats) * steps * world
+    h2d = sum(texts[k].numel() + sum(len(p) for p in g) for k, g in calls)
+    del hosts, pos_host
+    return {"value": round(scanned / dt / 1e9, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": steps, "calls_per_step": len(calls),
+            "api": "epsm_search_host (host text in, host positions out; its single searches "
+                   "run the same kernels as the device-timed value), pinned host buffers, "
+                   "wall clock"}
 
 
 def run_batched(ctx, torch, npairs):
@@ -386,145 +637,6 @@ def run_batched(ctx, torch, npairs):
             "graph_replay": ctx.batch_uses_graph, "counts_agree_with_per_pair": agree,
             "timing": "wall clock around the synchronous batched call (upload, launch, offsets "
                       "download) vs one asynchronous launch per pair and a final synchronize"}
-
-
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.case:
-        return run_case(args)
-    if args.sample:
-        return run_sample(args)
-
-    import torch
-    import gen
-    import paper_1209_6449_gb300 as epsm
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
-    else:
-        torch.cuda.set_device(0)
-    dev = torch.device(f"cuda:{local if world > 1 else 0}")
-    ctx = epsm.Context(dev.index)
-    stream = torch.cuda.current_stream()
-
-    # texts resident in HBM, generated on the device
-    texts = {}
-    for kind in KINDS:
-        t = torch.empty(TEXT_N, dtype=torch.uint8, device=dev)
-        gen.TextSpec(kind, 0).device(TEXT_N, t.data_ptr(), stream.cuda_stream)
-        texts[kind] = t
-    pats = workload_patterns(args.patterns)
-    nsearch = len(pats)
-    cap = TEXT_N // 8
-    out = torch.empty(cap, dtype=torch.int64, device=dev)
-    counts = torch.zeros(nsearch, dtype=torch.int64, device=dev)
-    torch.cuda.synchronize()
-
-    def step():
-        for i, (kind, m, p) in enumerate(pats):
-            ctx.search_async(texts[kind], p, out, cap, counts[i:i + 1], stream=stream)
-
-    launches0 = ctx.launch_count
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    st = ctx.sync()
-    if st != 0:
-        raise SystemExit(f"device status {st} after warm-up")
-    occ = counts.cpu().numpy()
-    assert int(occ.max()) <= cap, "output capacity exceeded"
-
-    clocks = ClockSampler(dev.index)
-    clocks.start()
-    time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    launches_before = ctx.launch_count
-    t_wall0 = time.time()
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_wall1 = time.time()
-    if dist:
-        dist.barrier()
-    launches = ctx.launch_count - launches_before
-    elapsed_ms = e0.elapsed_time(e1)
-    clocks.stop()
-    st = ctx.sync()
-    if st != 0:
-        raise SystemExit(f"device status {st} after timed region")
-    if dist:
-        tt = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
-
-    bytes_per_step = nsearch * TEXT_N
-    value = world * bytes_per_step * args.steps / (elapsed_ms / 1e3) / 1e9
-    occ_total = int(occ.sum())
-    # roofline of one search (the filter kernel and its emission kernel):
-    # algorithmic bytes = text read + 8 B per written position + 8 B count;
-    # duration = timed region / searches
-    alg_bytes_per_launch = (bytes_per_step + 8 * occ_total + 8 * nsearch) / nsearch
-    per_launch_s = elapsed_ms / 1e3 / max(args.steps * nsearch, 1)
-    achieved = alg_bytes_per_launch / per_launch_s / 1e9
-    peak, peak_kind = measured_peaks()
-    traffic = profiled_traffic()
-
-    e2e = None
-    cpu = None
-    if rank == 0 and not args.no_cpu:
-        cpu = oracle_sample(12.0, None)
-    if not args.no_e2e:
-        e2e = run_e2e(ctx, pats, args, torch, dev, dist)
-    batched = None
-    if not args.no_batch:
-        del texts, out
-        torch.cuda.empty_cache()
-        batched = run_batched(ctx, torch, args.batch_pairs)
-    served = None
-    if not args.no_serve and world == 1:
-        torch.cuda.empty_cache()
-        served = run_served(torch, args)
-
-    if rank == 0:
-        line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": round(elapsed_ms / args.steps, 3), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-                "config": config(args.patterns, world),
-                "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                             "unit": "GB/s", "frac": round(achieved / peak, 4),
-                             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                             "kernel": "stream_kernel + stream_emit_kernel, per search (all variants; "
-                                       "algorithmic bytes = n + 8*occ + 8 per search)",
-                             "traffic": traffic.get("bytes_per_launch") if traffic else None,
-                             "traffic_note": (traffic.get("note") if traffic else
-                                              "null: no ncu capture of the current kernel sources")},
-                "cpu_baseline": cpu,
-                "e2e": e2e,
-                "batched": batched,
-                "served": served,
-                "gpu_launches": launches,
-                "clocks": clocks.summary(t_wall0, t_wall1),
-                "occurrences_per_step": occ_total}
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
-    ctx.close()
-    return 0
 
 
 def run_served(torch, args):
@@ -608,52 +720,119 @@ def run_served(torch, args):
             "rates": out}
 
 
-def run_e2e(ctx, pats, args, torch, dev, dist):
-    """Same workload through epsm_search_host: host texts in, host positions out."""
-    import gen
-    from paper_1209_6449_gb300 import epsm_search_host
-    hosts = {}
-    for kind in KINDS:
-        h = torch.empty(TEXT_N, dtype=torch.uint8, pin_memory=True)
-        h.numpy()[:] = gen.TextSpec(kind, 0).host(TEXT_N)
-        hosts[kind] = h.numpy()
-    groups = {k: [p for (kk, m, p) in pats if kk == k] for k in KINDS}
-    # capacity per call: the largest per-text total seen on the device path
-    caps = {}
-    for k in KINDS:
-        st, offs = epsm_search_host(ctx.handle, hosts[k], groups[k],
-                                    np.zeros(0, dtype=np.uint64))
-        caps[k] = int(offs[-1])
-    cap = max(caps.values())
-    pos_host = torch.empty(max(cap, 1), dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
-    d2h = 0
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.case:
+        return run_case(args)
+    if args.sample:
+        return run_sample(args)
 
-    def step():
-        nonlocal d2h
-        d2h = 0
-        for k in KINDS:
-            st, offs = epsm_search_host(ctx.handle, hosts[k], groups[k], pos_host[:cap])
-            if st != 0:
-                raise SystemExit(f"epsm_search_host status {st}")
-            d2h += int(offs[-1]) * 8 + offs.size * 8
-    for _ in range(max(1, args.warmup)):
-        step()
+    import torch
+    import paper_1209_6449_gb300 as epsm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device(f"cuda:{local if world > 1 else 0}")
+    ctx = epsm.Context(dev.index)
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = measured_peaks()
+
+    if args.workload == "scan":
+        pats = scan_patterns()
+        texts = make_texts(torch, dev, SCAN_KINDS, SCAN_N, stream)
+        cfg, metric = scan_config(world), METRIC
+    else:
+        pats = sweep_patterns(args.patterns)
+        texts = make_texts(torch, dev, KINDS, TEXT_N, stream)
+        cfg, metric = sweep_config(args.patterns, world), SWEEP_METRIC
+    torch.cuda.synchronize()
+    res = measure(ctx, torch, texts, pats, args.steps, args.warmup, stream, dist, dev.index)
+    value = world * res["text_bytes_per_step"] * args.steps / (res["elapsed_ms"] / 1e3) / 1e9
+    nsearch = len(pats)
+    per_launch_s = res["elapsed_ms"] / 1e3 / max(args.steps * nsearch, 1)
+    alg_per_launch = res["alg_bytes_per_step"] / nsearch
+    achieved = alg_per_launch / per_launch_s / 1e9
+    traffic = profiled_traffic(args.workload)
+    rows = breakdown(pats, res, peak)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(ctx, torch, texts, pats, min(args.steps, 5), 1, res["occ"], dist)
+    del texts
+    torch.cuda.empty_cache()
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(args.workload)
+    sweep = None
+    if args.workload == "scan" and not args.no_sweep:
+        spats = sweep_patterns(args.patterns)
+        stexts = make_texts(torch, dev, KINDS, TEXT_N, stream)
+        sres = measure(ctx, torch, stexts, spats, max(1, args.steps // 2), args.warmup, stream, dist,
+                       dev.index)
+        del stexts
+        torch.cuda.empty_cache()
+        s_nsearch = len(spats)
+        s_alg = sres["alg_bytes_per_step"] / s_nsearch
+        s_per = sres["elapsed_ms"] / 1e3 / (sres["steps"] * s_nsearch)
+        sweep = {"metric": SWEEP_METRIC, "config": sweep_config(args.patterns, world),
+                 "value": round(world * sres["text_bytes_per_step"] * sres["steps"] /
+                                (sres["elapsed_ms"] / 1e3) / 1e9, 2),
+                 "unit": UNIT, "steps": sres["steps"],
+                 "ms_per_step": round(sres["elapsed_ms"] / sres["steps"], 3),
+                 "roofline": {"bound": "hbm", "achieved": round(s_alg / s_per / 1e9, 1),
+                              "peak": peak, "unit": "GB/s",
+                              "frac": round(s_alg / s_per / 1e9 / peak, 4)},
+                 "per_text_m": {k: {mk: v for mk, v in d.items()}
+                                for k, d in breakdown(spats, sres, peak).items()},
+                 "clocks": sres["clocks"]}
+    batched = None
+    if not args.no_batch:
+        batched = run_batched(ctx, torch, args.batch_pairs)
+    served = None
+    if not args.no_serve and world == 1:
+        torch.cuda.empty_cache()
+        served = run_served(torch, args)
+
+    if rank == 0:
+        line = {"metric": metric, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(res["elapsed_ms"] / args.steps, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+                "config": cfg,
+                "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                             "unit": "GB/s", "frac": round(achieved / peak, 4),
+                             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs: copy "
+                                            "bandwidth, burst)",
+                             "kernel": "one search (stream_kernel filter + stream_emit_kernel), "
+                                       "all variants; algorithmic bytes = n + 8*occ + 8 per search",
+                             "alg_bytes_per_launch": round(alg_per_launch),
+                             "traffic": traffic.get("bytes_per_launch") if traffic else None,
+                             "traffic_note": (traffic.get("note") if traffic else
+                                              "null: no ncu capture of the current kernel sources")},
+                "per_text_m": rows,
+                "cpu_baseline": cpu,
+                "e2e": e2e,
+                "sweep": sweep,
+                "batched": batched,
+                "served": served,
+                "gpu_launches": res["launches"],
+                "clocks": res["clocks"],
+                "occurrences_per_step": int(res["occ"].sum())}
+        print(json.dumps(line), flush=True)
     if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([dt], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dt = float(tt.item())
-    world = dist.get_world_size() if dist else 1
-    scanned = len(pats) * TEXT_N * args.steps * world
-    h2d = len(KINDS) * TEXT_N + sum(len(p) for (_, _, p) in pats)
-    return {"value": round(scanned / dt / 1e9, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "api": "epsm_search_host (one call per text, "
-                                              "pinned host buffers)"}
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
 
 
 if __name__ == "__main__":

@@ -259,10 +259,13 @@ class TextSpec:
         return uniform_table(MARKOV96)
 
     # -- host ---------------------------------------------------------------
-    def host(self, n: int, start: int = 0) -> np.ndarray:
-        """Bytes [start, start+n) of the text, made on the host."""
+    def host(self, n: int, start: int = 0, out: np.ndarray | None = None) -> np.ndarray:
+        """Bytes [start, start+n) of the text, made on the host (into ``out``,
+        a contiguous uint8 array of n bytes, when given)."""
         lib = _host_lib()
-        out = np.empty(n, dtype=np.uint8)
+        if out is None:
+            out = np.empty(n, dtype=np.uint8)
+        assert out.size == n and out.dtype == np.uint8 and out.flags["C_CONTIGUOUS"]
         if n == 0:
             return out
         k = key(self.seed, STREAM_TEXT)
@@ -276,6 +279,28 @@ class TextSpec:
             if self.kind == "dna_runs":
                 lib.gen_apply_runs(out.ctypes.data, start, n, key(self.seed, STREAM_RUNS),
                                    RUN_BLOCK, RUN_MAXLEN, ord("A"))
+        return out
+
+    def host_parallel(self, n: int, start: int = 0, threads: int | None = None,
+                      piece: int = 16 << 20) -> np.ndarray:
+        """``host`` made by several threads, each filling pieces of ``piece``
+        bytes (the byte streams are counter-based, so any range can be made
+        on its own; the C generator runs without the interpreter lock)."""
+        from concurrent.futures import ThreadPoolExecutor
+        out = np.empty(n, dtype=np.uint8)
+        if n == 0:
+            return out
+        if self.kind == "markov96":
+            _markov_cached(self.seed)   # build the tables once, before the threads
+        else:
+            _table_cached(self)
+
+        def work(a):
+            b = min(n, a + piece)
+            self.host(b - a, start=start + a, out=out[a:b])
+
+        with ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 1) as ex:
+            list(ex.map(work, range(0, n, piece)))
         return out
 
     # -- device -------------------------------------------------------------

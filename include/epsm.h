@@ -148,20 +148,20 @@ epsm_status epsm_search_batch(epsm_ctx *ctx, uint32_t npairs,
                               uint64_t *positions, uint64_t capacity,
                               uint64_t *offsets, void *stream);
 
-/* End-to-end search from HOST memory: copies the text to the device, searches
- * it for `npat` patterns in one batched launch, and copies the results back.
+/* End-to-end search from HOST memory: copies the text to the device, runs one
+ * single search (the kernels of epsm_search, automatic variant) per pattern
+ * on it, and copies the positions back.
  *   text_host      host, n bytes
  *   patterns_host  host, concatenation of the npat patterns
- *   ms             host, npat pattern lengths (each 1..32)
- *   positions_host host, room for `capacity` uint64
+ *   ms             host, npat pattern lengths (each 1..EPSM_MAX_M_LONG)
+ *   positions_host host, room for `capacity` uint64 (pinned memory makes the
+ *                  copy faster)
  *   offsets_host   host, npat+1 entries (pattern k's positions are at
  *                  [offsets[k], offsets[k+1]); offsets[npat] = total)
- * Synchronous. */
-epsm_status epsm_search_host(epsm_ctx *ctx, const uint8_t *text_host, uint64_t n,
-                             const uint8_t *patterns_host, const uint32_t *ms, uint32_t npat,
-                             uint64_t *positions_host, uint64_t capacity,
-                             uint64_t *offsets_host);
-
+ * Synchronous.  Device staging for the text and `capacity` positions lives in
+ * the context (grown on demand).  If the total exceeds `capacity`, the first
+ * `capacity` positions are copied, the offsets are the true ones, and the call
+ * returns EPSM_ERR_CAPACITY. */
 /* Variant the context uses for pattern length m under EPSM_VARIANT_AUTO. */
 int epsm_variant_for(epsm_ctx *ctx, uint32_t m);
 
@@ -185,10 +185,12 @@ int epsm_batch_uses_graph(epsm_ctx *ctx);
  * The paper has no counterpart: this entry point exists for callers that may
  * not allocate device memory themselves (a framework that routes every
  * allocation through its own pool, a real-time loop where an allocation could
- * stall or fail, a plug-in whose host pre-sizes all memory).  The search is the
- * same as epsm_search_async with the automatic variant; its scratch lives in a
- * fixed device array of about 8.5 MiB inside the library, which every GPU that
- * loads the library keeps until the process exits.
+ * stall or fail, a plug-in whose host pre-sizes all memory).  The search runs
+ * the kernels of epsm_search_async with the library's built-in per-m variant
+ * choice (a context may have installed a measured table instead; the positions
+ * are the same, the speed can differ); its scratch lives in a fixed device
+ * array of about 8.5 MiB inside the library, which every GPU that loads the
+ * library keeps until the process exits.
  *   text        device, n bytes, n <= EPSM_STATIC_MAX_TEXT (larger n returns
  *               EPSM_ERR_ARG without touching the GPU)
  *   pattern     host, m bytes (1..32)
@@ -198,10 +200,11 @@ int epsm_batch_uses_graph(epsm_ctx *ctx);
  *               capacity); both are cleared when the call is enqueued
  * Asynchronous on `stream` (NULL = default stream) on the current device.
  * The first call on a device looks up the array's device address and the SM
- * count; make that first call before any stream capture.  Calls share the one
- * array: calls whose work overlaps on the GPU (different streams, or another
- * host thread) race and give wrong results; order them on one stream.  It
- * calls no cudaMalloc, cudaFree or other allocating routine. */
+ * count and clears the array's counters, waiting on `stream` for the clearing
+ * to complete; make that first call before any stream capture.  Calls share
+ * the one array: calls whose work overlaps on the GPU (different streams, or
+ * another host thread) race and give wrong results; order them on one stream.
+ * It calls no cudaMalloc, cudaFree or other allocating routine. */
 epsm_status epsm_search_static(const uint8_t *text, uint64_t n, const uint8_t *pattern,
                                uint32_t m, uint64_t *positions, uint64_t capacity,
                                uint64_t *result_dev, void *stream);

@@ -114,19 +114,3 @@ def kmp_count(text, pattern) -> int:
     if m == 0 or m > n:
         return 0
     return int(lib.oracle_kmp_count(_ptr(t), n, _ptr(p), m))
-
-
-def search_at(text, pattern, starts) -> np.ndarray:
-    """Boolean per requested start: does ``pattern`` occur at that start?
-
-    Used to check sampled outputs of very large runs one by one.
-    """
-    t = _as_u8(text)
-    p = _as_u8(pattern)
-    m = int(p.size)
-    res = np.zeros(len(starts), dtype=bool)
-    for k, s in enumerate(starts):
-        s = int(s)
-        if 0 <= s and s + m <= t.size:
-            res[k] = bool(np.array_equal(t[s:s + m], p))
-    return res

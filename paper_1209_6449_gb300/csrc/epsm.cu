@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -25,16 +26,59 @@ using namespace epsm;
 
 namespace {
 constexpr uint32_t kMaxRanges = 16384;  // range-total scratch of a context (emit ranges)
+constexpr int kMaxDevices = 64;         // devices the per-device caches below cover
+
+// Resident blocks per SM of `kernel` on the CURRENT device, worked out once
+// per device: the dynamic shared-memory opt-in (cudaFuncSetAttribute) belongs
+// to a device's context, so a second device needs its own set-up.  `cache`
+// holds one entry per device (0: not yet known); concurrent first calls on a
+// device may both do the set-up, which is harmless.  Returns 0 on a CUDA
+// error or a device index beyond the cache.
+template <typename K>
+int blocks_per_sm(K kernel, int threads, size_t smem, int cap, std::atomic<int> (&cache)[kMaxDevices]) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+    const int known = cache[dev].load(std::memory_order_acquire);
+    if (known > 0) return known;
+    if (smem > 0 && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem) != cudaSuccess)
+        return 0;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, smem) != cudaSuccess) return 0;
+    const int v = std::max(1, cap > 0 ? std::min(b, cap) : b);
+    cache[dev].store(v, std::memory_order_release);
+    return v;
+}
+
+// Makes a context's device current for the duration of a call and restores
+// the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; prev = -1; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
 }
 
 #define EPSM_API extern "C" __attribute__((visibility("default")))
 
 namespace {
 
+// Built-in per-m choice (a context may install a measured table instead):
+// the packed compare for m <= 4, the adaptive 4-byte block / 2-bit code filter
+// up to 16, the 8-byte block fingerprint above, with the block stride for
+// m >= 23.
 int default_variant(uint32_t m) {
     if (m <= 4) return V_DIRECT;
-    if (m <= 14) return V_ADAPT;
-    return V_BLOCK8;
+    if (m <= 16) return V_ADAPT;
+    if (m <= 22) return V_BLOCK8;
+    return V_BLOCK8S;
 }
 
 bool variant_covers(int v, uint32_t m) {
@@ -218,33 +262,19 @@ epsm_status ensure_stream_scratch(epsm_ctx *c, uint64_t nstages, cudaStream_t s)
 // segments (32 stages); for a count only, a single one.
 
 int stream_emit_grid(int sms) {
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stream_emit_kernel, stream::kEmitThreads, 0) !=
-            cudaSuccess)
-            return 0;
-        per_sm = std::max(1, b);
-    }
-    return sms * per_sm;
+    static std::atomic<int> cache[kMaxDevices];
+    return sms * blocks_per_sm(stream_emit_kernel, stream::kEmitThreads, 0, 0, cache);
 }
 
 // A single search: the streaming filter kernel (epsm_stream.cuh; up to two
 // blocks per SM), then, when positions are wanted, the emission kernel.
 template <int V, int MP>
 cudaError_t launch_stream_t(int sms, stream::StreamParams &p, cudaStream_t s) {
-    static int per_sm = 0;
+    static std::atomic<int> cache[kMaxDevices];
     const size_t smem = sizeof(stream::StreamSmem);
-    if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(stream_kernel<V, MP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, stream_kernel<V, MP>,
-                                                          stream::kThreadsStream, smem);
-        if (e != cudaSuccess) return e;
-        per_sm = std::max(1, std::min(b, stream::kMaxBlocksPerSm));
-    }
+    const int per_sm = blocks_per_sm(stream_kernel<V, MP>, stream::kThreadsStream, smem,
+                                     stream::kMaxBlocksPerSm, cache);
+    if (per_sm == 0) return cudaErrorInvalidDevice;
     uint64_t grid = std::min<uint64_t>(std::max<uint64_t>(p.nstages, 1u), (uint64_t)sms * per_sm);
     grid = std::min<uint64_t>(grid, stream::kMaxBlocks);
     const uint64_t nst = std::max<uint64_t>(p.nstages, 1u);
@@ -392,32 +422,16 @@ void free_batch(BatchRes &R) {
 }
 
 int batch_grid(int sms) {
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        const size_t smem = sizeof(group::Smem);
-        if (cudaFuncSetAttribute(group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
-            return 0;
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, group_kernel, stream::kThreadsStream,
-                                                          smem) != cudaSuccess)
-            return 0;
-        per_sm = std::max(1, std::min(b, stream::kMaxBlocksPerSm));
-    }
+    static std::atomic<int> cache[kMaxDevices];
+    const int per_sm = blocks_per_sm(group_kernel, stream::kThreadsStream, sizeof(group::Smem),
+                                     stream::kMaxBlocksPerSm, cache);
     return (int)std::min<uint64_t>((uint64_t)sms * per_sm, stream::kMaxBlocks);
 }
 
 // Blocks of the emission kernel: as many as fit (it is latency bound).
 int emit_grid(int sms) {
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, group_emit_kernel, stream::kEmitThreads, 0) !=
-            cudaSuccess)
-            return 0;
-        per_sm = std::max(1, b);
-    }
-    return sms * per_sm;
+    static std::atomic<int> cache[kMaxDevices];
+    return sms * blocks_per_sm(group_emit_kernel, stream::kEmitThreads, 0, 0, cache);
 }
 
 void drop_graph(BatchRes &R) {
@@ -915,6 +929,9 @@ EPSM_API const char *epsm_last_error(epsm_ctx *c) { return c ? c->errbuf : ""; }
 EPSM_API epsm_status epsm_search_async(epsm_ctx *c, const uint8_t *text, uint64_t n,
                                        const uint8_t *pattern, uint32_t m, uint64_t *positions,
                                        uint64_t capacity, uint64_t *count_dev, void *stream) {
+    if (!c) return EPSM_ERR_ARG;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return EPSM_ERR_CUDA;
     return search_async_impl(c, EPSM_VARIANT_AUTO, text, n, pattern, m, positions, capacity,
                              count_dev, stream, 0);
 }
@@ -923,6 +940,9 @@ EPSM_API epsm_status epsm_search_variant(epsm_ctx *c, int variant, const uint8_t
                                          uint64_t n, const uint8_t *pattern, uint32_t m,
                                          uint64_t *positions, uint64_t capacity,
                                          uint64_t *count_dev, void *stream) {
+    if (!c) return EPSM_ERR_ARG;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return EPSM_ERR_CUDA;
     return search_async_impl(c, variant, text, n, pattern, m, positions, capacity, count_dev,
                              stream, 0);
 }
@@ -931,6 +951,8 @@ EPSM_API epsm_status epsm_search(epsm_ctx *c, const uint8_t *text, uint64_t n,
                                  const uint8_t *pattern, uint32_t m, uint64_t *positions,
                                  uint64_t capacity, uint64_t *count, void *stream) {
     if (!c || !count) return EPSM_ERR_ARG;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return EPSM_ERR_CUDA;
     epsm_status st = search_async_impl(c, EPSM_VARIANT_AUTO, text, n, pattern, m, positions,
                                        capacity, &c->misc->count, stream, 0);
     if (st != EPSM_OK) return st;
@@ -961,6 +983,8 @@ __global__ void wait_probe_kernel(const uint32_t *flag, uint32_t *err, uint64_t 
 
 EPSM_API epsm_status epsm_wait_probe(epsm_ctx *c, uint64_t limit_ns, void *stream) {
     if (!c || limit_ns == 0 || limit_ns > 1000000000ull) return EPSM_ERR_ARG;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return EPSM_ERR_CUDA;
     cudaStream_t s = pick_stream(c, stream);
     epsm_status st = order_after_previous(c, s);
     if (st != EPSM_OK) return st;
@@ -974,6 +998,8 @@ EPSM_API epsm_status epsm_wait_probe(epsm_ctx *c, uint64_t limit_ns, void *strea
 
 EPSM_API epsm_status epsm_sync(epsm_ctx *c, void *stream) {
     if (!c) return EPSM_ERR_ARG;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return EPSM_ERR_CUDA;
     uint32_t err = 0;
     epsm_status st = read_misc(c, pick_stream(c, stream), &err);
     if (st != EPSM_OK) return st;
@@ -993,6 +1019,8 @@ EPSM_API epsm_status epsm_search_batch(epsm_ctx *c, uint32_t npairs, const uint8
     }
     if (!texts || !ns || !patterns || !ms) return EPSM_ERR_ARG;
     if (capacity > 0 && !positions) return EPSM_ERR_ARG;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return EPSM_ERR_CUDA;
     for (uint32_t i = 0; i < npairs; ++i) {
         if (ms[i] == 0 || ms[i] > EPSM_MAX_M || !patterns[i]) return EPSM_ERR_ARG;
         if (ns[i] > 0 && !texts[i]) return EPSM_ERR_ARG;
@@ -1008,6 +1036,10 @@ EPSM_API epsm_status epsm_search_host(epsm_ctx *c, const uint8_t *text_host, uin
     if (!c || !offsets_host || (n > 0 && !text_host)) return EPSM_ERR_ARG;
     if (npat > 0 && (!patterns_host || !ms)) return EPSM_ERR_ARG;
     if (capacity > 0 && !positions_host) return EPSM_ERR_ARG;
+    for (uint32_t k = 0; k < npat; ++k)
+        if (ms[k] == 0 || ms[k] > EPSM_MAX_M_LONG) return EPSM_ERR_ARG;
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return EPSM_ERR_CUDA;
     cudaStream_t s = c->stream;
     if (n + 16 > c->dtext_cap) {
         CK(cudaStreamSynchronize(s));
@@ -1028,28 +1060,30 @@ EPSM_API epsm_status epsm_search_host(epsm_ctx *c, const uint8_t *text_host, uin
     epsm_status st = order_after_previous(c, s);
     if (st != EPSM_OK) return st;
     if (n) CK(cudaMemcpyAsync(c->dtext, text_host, n, cudaMemcpyHostToDevice, s));
-    std::vector<const uint8_t *> texts(npat, c->dtext), pats(npat);
-    std::vector<uint64_t> ns(npat, n);
+    // one single search per pattern (the kernels of epsm_search), each writing
+    // its positions right after the previous pattern's; the count comes back
+    // after each search, and the positions are copied back once at the end
     uint64_t off = 0;
+    uint64_t p0 = 0;
     for (uint32_t k = 0; k < npat; ++k) {
-        if (ms[k] == 0 || ms[k] > EPSM_MAX_M) return EPSM_ERR_ARG;
-        pats[k] = patterns_host + off;
-        off += ms[k];
+        offsets_host[k] = off;
+        const uint64_t room = off < capacity ? capacity - off : 0;
+        st = search_async_impl(c, EPSM_VARIANT_AUTO, c->dtext, n, patterns_host + p0, ms[k],
+                               room ? c->dpos + off : nullptr, room, &c->misc->count, s, 0);
+        if (st != EPSM_OK) return st;
+        uint32_t err = 0;
+        if ((st = read_misc(c, s, &err)) != EPSM_OK) return st;
+        if (err & kErrTimeout) return EPSM_ERR_TIMEOUT;
+        off += c->hmisc->count;
+        p0 += ms[k];
     }
-    if (npat == 0) {
-        offsets_host[0] = 0;
-        return mark_done(c, s);
-    }
-    st = batch_impl(c, npat, texts.data(), ns.data(), pats.data(), ms, c->dpos, capacity,
-                    offsets_host, s);
-    if (st != EPSM_OK && st != EPSM_ERR_CAPACITY) return st;
-    uint64_t got = std::min<uint64_t>(offsets_host[npat], capacity);
+    offsets_host[npat] = off;
+    const uint64_t got = std::min<uint64_t>(off, capacity);
     if (got) {
-        CK(cudaMemcpyAsync(positions_host, c->dpos, got * sizeof(uint64_t),
-                           cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(positions_host, c->dpos, got * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
     }
-    return st;
+    return off > capacity ? EPSM_ERR_CAPACITY : EPSM_OK;
 }
 
 EPSM_API int epsm_variant_for(epsm_ctx *c, uint32_t m) {
@@ -1084,8 +1118,9 @@ EPSM_API int epsm_batch_uses_graph(epsm_ctx *c) {
 
 namespace {
 
+// stages_for: (delta + n - m - off) / stage + 1 with delta <= 15 and off >= -15
 constexpr uint64_t kStaticMaxStages =
-    (EPSM_STATIC_MAX_TEXT + 15u + 7u) / stream::kStageBytes + 1u;
+    (EPSM_STATIC_MAX_TEXT + 15u + 15u) / stream::kStageBytes + 1u;
 constexpr uint64_t kStaticMaxSegs = kStaticMaxStages * stream::kConsumerWarps;
 constexpr uint64_t kStaticCountBytes = kStaticMaxSegs * sizeof(uint32_t);
 constexpr uint64_t kStaticMaskBytes = kStaticMaxSegs * stream::kSegChunks * sizeof(uint16_t);
@@ -1129,24 +1164,27 @@ EPSM_API epsm_status epsm_search_static(const uint8_t *text, uint64_t n, const u
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return EPSM_ERR_CUDA;
-        // the claim ticket, done and barrier counters and the range totals
-        // must start at zero
-        if (cudaMemsetAsync(ptr, 0, kStaticMiscBytes, s) != cudaSuccess) return EPSM_ERR_CUDA;
+        // the claim tickets, done counters and range totals must start at
+        // zero; the clearing completes before the device is marked ready, so
+        // a first call on one stream cannot race a later call on another
+        if (cudaMemsetAsync(ptr, 0, kStaticMiscBytes, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return EPSM_ERR_CUDA;
         D.base = static_cast<uint8_t *>(ptr) + kStaticMiscBytes;
         D.misc = static_cast<DevMisc *>(ptr);
         D.sms = sms;
         D.ready = true;
     }
-    // result_dev[0] = count, result_dev[1] = device error bits; the error word
-    // must start at zero
-    if (cudaMemsetAsync(result_dev, 0, 2 * sizeof(uint64_t), s) != cudaSuccess) return EPSM_ERR_CUDA;
     const int v = default_variant(m);
-    if (n < m) return EPSM_OK;
     stream::StreamParams p;
     memset(&p, 0, sizeof(p));
     p.job = make_job(text, n, pack_pattern(pattern, m));
     p.nstages = stages_for(p.job.delta, n, m, v);
-    if (p.nstages > kStaticMaxStages) return EPSM_ERR_ARG;
+    if (p.nstages > kStaticMaxStages) return EPSM_ERR_ARG;  // (cannot happen for n <= the maximum)
+    // result_dev[0] = count, result_dev[1] = device error bits; the error word
+    // must start at zero
+    if (cudaMemsetAsync(result_dev, 0, 2 * sizeof(uint64_t), s) != cudaSuccess) return EPSM_ERR_CUDA;
+    if (n < m) return EPSM_OK;
     p.chunk_full0 = (p.job.delta + 15u) / 16u;
     p.chunk_full1 = p.job.lim / 16u;
     p.emit = capacity > 0 ? 1 : 0;
