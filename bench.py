@@ -77,7 +77,8 @@ def parse():
                     help="sweep: patterns per (text, m); the workload uses 100")
     ap.add_argument("--case", default=None,
                     help="KIND:M[:VARIANT[:N[:MODE]]] -- time one search of an N-byte text "
-                         "(default 256 MiB) and exit (the small cases of ncu captures); MODE "
+                         "(default 256 MiB; a count-only search first sizes the output) and "
+                         "exit (the small cases of ncu captures); MODE "
                          "'count': count only; 'iid': an i.i.d. pattern instead of a planted "
                          "one; 'runs': the pattern A^m")
     ap.add_argument("--reps", type=int, default=3)
@@ -115,9 +116,12 @@ def run_case(args):
         pat = gen.random_patterns(spec, m, 1)[0]
     else:
         pat = gen.planted_patterns(spec, n, m, 1)[0]
-    cap = 0 if mode == "count" else n // 3
-    out = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    # a count-only search first sizes the output (the first launch of a case)
+    ctx.search_async(t, pat, cnt, 0, cnt, variant=variant)
+    torch.cuda.synchronize()
+    cap = 0 if mode == "count" else int(cnt.item()) + 1024
+    out = torch.empty(max(cap, 1), dtype=torch.int64, device="cuda")
     times = []
     for _ in range(args.reps):
         e0 = torch.cuda.Event(enable_timing=True)

@@ -107,6 +107,21 @@ Pattern pack_pattern(const uint8_t *p, uint32_t m) {
         pat.w[i] = (uint32_t)bytes[4 * i] | ((uint32_t)bytes[4 * i + 1] << 8) |
                    ((uint32_t)bytes[4 * i + 2] << 16) | ((uint32_t)bytes[4 * i + 3] << 24);
     pat.m = m;
+    pat.kbits = kHashBitsDefault;
+    // smallest period up to 8 (the block variants' run shortcut), and the
+    // last 8 bytes
+    pat.q = 0;
+    for (uint32_t q = 1; q <= 8 && q < m; ++q) {
+        uint32_t i = 0;
+        while (i + q < m && p[i] == p[i + q]) ++i;
+        if (i + q == m) { pat.q = q; break; }
+    }
+    if (m >= 8) {
+        uint8_t t8[8];
+        memcpy(t8, p + m - 8, 8);
+        pat.tl = (uint32_t)t8[0] | ((uint32_t)t8[1] << 8) | ((uint32_t)t8[2] << 16) | ((uint32_t)t8[3] << 24);
+        pat.th = (uint32_t)t8[4] | ((uint32_t)t8[5] << 8) | ((uint32_t)t8[6] << 16) | ((uint32_t)t8[7] << 24);
+    }
     return pat;
 }
 
@@ -358,6 +373,7 @@ epsm_status search_async_impl(epsm_ctx *c, int variant, const uint8_t *text, uin
     p.job = make_job(text, n, pack_pattern(pattern, longp ? EPSM_MAX_M : m));
     if (longp) {
         p.job.pmax = (int64_t)(p.job.delta + n) - (int64_t)m;
+        p.job.pat.q = 0;  // (the period shortcut covers patterns of at most 32 bytes)
         const uint32_t mt = m - EPSM_MAX_M;
         if (mt > c->tail_cap) {
             CK(cudaStreamSynchronize(s));

@@ -136,7 +136,8 @@ struct Params {
     const Header *hdr;
     const JobDesc *jobs;
     GroupTables *comb;           // one per group of more than one pattern
-    uint8_t *tables;             // block-variant tables of individual patterns (kTableBytes each)
+    uint8_t *tables;             // block-variant tables of individual patterns (kTableBytes each:
+                                 // the fingerprint bit table, then the 8 pattern blocks)
     uint64_t *offsets;           // per job: exclusive prefix at its first segment; [njobs] = total
     uint32_t *seg_count;         // per pattern segment: hits
     uint32_t *seg_off;           // per pattern segment with hits: its list in pool
@@ -147,7 +148,7 @@ struct Params {
     DevMisc *misc;
 };
 
-constexpr int kTableBytes = kHashSlots + 16 * 4;
+constexpr int kTableBytes = kTableWords * 4 + 16 * 4;
 
 // What a warp needs to check a candidate in full.
 struct VCtx {
@@ -233,17 +234,18 @@ __global__ void build_group_tables_kernel(const Params P) {
         if (D.table == kNone) continue;
         uint8_t *tb = P.tables + (uint64_t)D.table * kTableBytes;
         uint32_t *tw = reinterpret_cast<uint32_t *>(tb);
-        for (int i = threadIdx.x; i < kHashSlots / 4; i += blockDim.x) tw[i] = 0u;
+        for (int i = threadIdx.x; i < kTableWords; i += blockDim.x) tw[i] = 0u;
         __syncthreads();
         if (threadIdx.x < 8) {
             const int q = threadIdx.x >> 2;
             const uint32_t sh = 8u * (uint32_t)(threadIdx.x & 3);
             const uint32_t lo = __funnelshift_r(D.job.pat.w[q], D.job.pat.w[q + 1], sh);
             const uint32_t hi = __funnelshift_r(D.job.pat.w[q + 1], D.job.pat.w[q + 2], sh);
-            uint32_t *pb = reinterpret_cast<uint32_t *>(tb + kHashSlots);
+            uint32_t *pb = tw + kTableWords;
             pb[2 * threadIdx.x] = lo;
             pb[2 * threadIdx.x + 1] = hi;
-            tb[block_hash(lo, hi)] = 1;
+            const uint32_t h = block_hash(lo, hi, D.job.pat.kbits);
+            atomicOr(&tw[h >> 5], 1u << (h & 31u));
         }
         __syncthreads();
     }
@@ -475,8 +477,10 @@ __device__ __noinline__ void plain_job(const Params &P, const Header &H, Smem &S
                                        const uint8_t *buf, uint64_t ls, int w, int lane) {
     const uint64_t c0 = ls * kStageChunks;
     const BcastWords Bw(D.job.pat);
-    const uint8_t *tb = D.table == kNone ? nullptr : P.tables + (uint64_t)D.table * kTableBytes;
-    const uint32_t *pb = tb ? reinterpret_cast<const uint32_t *>(tb + kHashSlots) : nullptr;
+    const uint32_t *tb = D.table == kNone
+                             ? nullptr
+                             : reinterpret_cast<const uint32_t *>(P.tables + (uint64_t)D.table * kTableBytes);
+    const uint32_t *pb = tb ? tb + kTableWords : nullptr;
     const uint64_t cf0 = (D.job.delta + 15u) / 16u, cf1 = D.job.lim / 16u;
     uint32_t h[4] = {0u, 0u, 0u, 0u};
     bool dense = false;  // the adaptive variant probes every segment here

@@ -41,9 +41,13 @@ constexpr int V_CODE2 = 6;
 constexpr int V_ADAPT = 7;
 constexpr int V_BLOCK8S = 8;
 
-// Block fingerprint table (Section 3.4): k = 11 bits -> 2048 one-byte slots.
-constexpr int kHashBits = 11;
-constexpr int kHashSlots = 1 << kHashBits;
+// Block fingerprint table (Section 3.4): a bit table of 2^k slots.  The paper
+// takes k = 11; here k is a parameter of the search (1 <= k <= kHashBitsMax,
+// default kHashBitsDefault): a wider table makes false fingerprint matches of
+// the text's blocks rarer at no cost in shared memory (2^14 bits = 2 KiB).
+constexpr int kHashBitsMax = 14;
+constexpr int kHashBitsDefault = 14;
+constexpr int kTableWords = (1 << kHashBitsMax) / 32;  // uint32 words of the bit table
 
 // Error bits of the device error word.
 constexpr uint32_t kErrTimeout = 1u;   // a look-back wait gave up
@@ -52,6 +56,14 @@ constexpr uint32_t kErrCapacity = 2u;  // an occurrence did not fit in the outpu
 struct Pattern {
     uint32_t w[8];  // p packed little-endian, zero padded (the paper's blocks P_i, Section 2)
     uint32_t m;
+    // Smallest period q of p (p[i] == p[i+q] for all i < m-q) when q <= 8 and
+    // m <= 32, else 0.  If s is an occurrence, s+q is one iff the text's bytes
+    // [s+m-q, s+m) equal p's last q bytes (the other m-q already match by
+    // periodicity); the block variants use this to confirm the candidates of
+    // a run in one 8-byte compare each.
+    uint32_t q;
+    uint32_t tl, th;  // p's last 8 bytes (m >= 8), little-endian
+    uint32_t kbits;   // fingerprint width k of the block variants' table
 };
 
 struct SearchJob {
@@ -172,9 +184,14 @@ __device__ __forceinline__ uint32_t bcast_byte(uint32_t w, int j) {
     return __byte_perm(w, 0u, (uint32_t)(j * 0x1111));
 }
 
-// Multiplicative (Fibonacci) hash of an 8-byte block to kHashBits bits.
-__device__ __forceinline__ uint32_t block_hash(uint32_t lo, uint32_t hi) {
-    return (lo * 0x9E3779B1u + hi * 0x85EBCA77u) >> (32 - kHashBits);
+// Multiplicative (Fibonacci) hash of an 8-byte block to k bits (1 <= k <= 14).
+__device__ __forceinline__ uint32_t block_hash(uint32_t lo, uint32_t hi, uint32_t k) {
+    return (lo * 0x9E3779B1u + hi * 0x85EBCA77u) >> (32u - k);
+}
+
+// Slot h of a fingerprint bit table.
+__device__ __forceinline__ uint32_t table_bit(const uint32_t *table, uint32_t h) {
+    return (table[h >> 5] >> (h & 31u)) & 1u;
 }
 
 // Mask of the bytes of pattern word i that belong to the pattern.
@@ -238,6 +255,29 @@ __device__ __forceinline__ bool verify_staged(const SearchJob &J, int64_t P, con
         return true;
     }
     return verify_global(J, P);
+}
+
+// The text's bytes [P+m-8, P+m) against p's last 8 bytes (m >= 8), read from
+// the staged bytes when they cover them, else from global memory.  With P-q
+// an occurrence and q <= 8 a period of p, this decides whether P is one.
+__device__ __forceinline__ bool tail8_ok(const SearchJob &J, int64_t P, const StagedText &T) {
+    const int64_t a = P + (int64_t)J.pat.m - 8;
+    const int64_t o = a - T.sbase;
+    uint32_t x0, x1, x2;
+    const uint32_t sh = ((uint32_t)a & 3u) * 8u;
+    if (T.inside && o >= 0 && o + 8 <= (int64_t)T.span) {
+        const uint32_t *W = reinterpret_cast<const uint32_t *>(T.buf);
+        const uint32_t wa = (uint32_t)o >> 2;  // (sbase is 16-byte aligned)
+        x0 = W[wa];
+        x1 = W[wa + 1];
+        x2 = sh ? W[wa + 2] : 0u;
+    } else {
+        const uint64_t wa = (uint64_t)a >> 2;
+        x0 = load_word(J, wa);
+        x1 = load_word(J, wa + 1);
+        x2 = sh ? load_word(J, wa + 2) : 0u;
+    }
+    return __funnelshift_r(x0, x1, sh) == J.pat.tl && __funnelshift_r(x1, x2, sh) == J.pat.th;
 }
 
 // ---------------------------------------------------------------------------

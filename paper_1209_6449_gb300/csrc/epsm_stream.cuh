@@ -46,6 +46,19 @@ constexpr int kMaxBlocksPerSm = 2;
 constexpr uint64_t kMaxBlocks = 512;                        // grid bound (range totals, status words)
 
 constexpr uint32_t kClaim = 2;                              // stages per claim
+
+// A segment's count word: its hits in the low 16 bits (at most 2048) and, when
+// its hits are stored as chunk records, the number of records in the high 16
+// bits (0: stored as the 128 chunk masks).  A record is chunk << 16 | mask for
+// a chunk with hits, in chunk order; segments with at most kRecMax chunks with
+// hits use records (4 bytes per such chunk instead of 256 bytes of masks).
+constexpr uint32_t kCountMask = 0xFFFFu;
+constexpr uint32_t kRecMax = 32;
+// Records pay off where chunks with hits carry several each (runs) or where
+// there are few; a segment of scattered single hits expands faster from masks.
+__device__ __forceinline__ bool use_records(uint32_t hits, uint32_t nz) {
+    return nz <= kRecMax && (nz <= 8u || hits >= 2u * nz);
+}
 constexpr int kAdaptDense = 2;   // probe: steps of 4 with a block match somewhere => dense text
 constexpr uint64_t kEndStage = ~0ull;
 
@@ -57,7 +70,7 @@ struct alignas(128) StreamSmem {
     uint64_t full[kStages];
     uint64_t empty[kStages];
     uint32_t pblk[32];
-    uint8_t table[kHashSlots];
+    uint32_t table[kTableWords];  // block fingerprint bit table
 };
 
 // ---------------------------------------------------------------------------
@@ -193,7 +206,10 @@ __device__ __forceinline__ void flush_slot(const StreamParams &P, StreamSmem &S,
     uint4 *dst = reinterpret_cast<uint4 *>(P.seg_count + st * kConsumerWarps);
     dst[0] = a;
     dst[1] = b;
-    const uint32_t tot = a.x + a.y + a.z + a.w + b.x + b.y + b.z + b.w;
+    const uint32_t tot = ((a.x & kCountMask) + (a.y & kCountMask) + (a.z & kCountMask) +
+                          (a.w & kCountMask)) +
+                         ((b.x & kCountMask) + (b.y & kCountMask) + (b.z & kCountMask) +
+                          (b.w & kCountMask));
     if (tot) atomicAdd(&P.range_total[st / P.range_stages], (unsigned long long)tot);
 }
 
@@ -287,7 +303,7 @@ __device__ __forceinline__ void load_segment(const SearchJob &J, uint64_t cf0, u
 template <int V, int MP>
 __device__ __forceinline__ uint32_t segment_hits(const SearchJob &J, const uint4 (&ch)[4], const uint4 halo,
                                                  int64_t sp0, bool interior, const BcastWords &B,
-                                                 const uint8_t *table, const uint32_t *pblk,
+                                                 const uint32_t *table, const uint32_t *pblk,
                                                  const StagedText &T, int lane, uint32_t (&h)[4]) {
     uint32_t cnt = 0u;
     if constexpr (V == V_CODE2) {
@@ -368,7 +384,7 @@ __device__ __forceinline__ uint32_t segment_hits(const SearchJob &J, const uint4
 //   so, else with the 4-byte block filter (m >= 7) or the prefix filter.
 template <int V, int MP, bool PROBE = false>
 __device__ __forceinline__ uint32_t stage_hits(const SearchJob &J, uint64_t cf0, uint64_t cf1,
-                                               const BcastWords &B, const uint8_t *table,
+                                               const BcastWords &B, const uint32_t *table,
                                                const uint32_t *pblk, const uint8_t *buf,
                                                uint64_t c0, int w, int lane, uint32_t (&h)[4],
                                                bool *dense_out = nullptr, const uint8_t *tail = nullptr,
@@ -415,16 +431,37 @@ __device__ __forceinline__ uint32_t stage_hits(const SearchJob &J, uint64_t cf0,
 __device__ __forceinline__ void store_segment(const StreamParams &P, uint32_t *wslot, uint64_t seg,
                                               uint32_t cnt, const uint32_t (&h)[4], int lane,
                                               uint64_t &acc) {
-    const uint32_t wc = __any_sync(kFull, cnt != 0u) ? warp_sum(cnt) : 0u;
+    if (!__any_sync(kFull, cnt != 0u)) {
+        if (P.emit && lane == 0) *wslot = 0u;
+        return;
+    }
+    const uint32_t wc = warp_sum(cnt);
     if (!P.emit) {  // count only: the warp adds its total once, at the end
         acc += wc;
         return;
     }
-    if (lane == 0) *wslot = wc;
-    if (wc != 0u) {
+    uint32_t bal[4], nz = 0u;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        bal[u] = __ballot_sync(kFull, h[u] != 0u);
+        nz += __popc(bal[u]);
+    }
+    if (use_records(wc, nz)) {
+        // chunk records in chunk order (chunk 32u + lane)
+        uint32_t *rec = reinterpret_cast<uint32_t *>(P.seg_mask + seg * kSegChunks);
+        const uint32_t below = (1u << lane) - 1u;
+        uint32_t off = 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (h[u]) rec[off + __popc(bal[u] & below)] = ((uint32_t)(32 * u + lane) << 16) | h[u];
+            off += __popc(bal[u]);
+        }
+        if (lane == 0) *wslot = wc | (nz << 16);
+    } else {
         uint16_t *m = P.seg_mask + seg * kSegChunks;
 #pragma unroll
         for (int u = 0; u < 4; ++u) m[32 * u + lane] = (uint16_t)h[u];
+        if (lane == 0) *wslot = wc;
     }
 }
 
@@ -624,9 +661,86 @@ struct alignas(16) StreamEmitSmem {
     uint32_t claim;
 };
 
+// Emission of the record-format segments among a warp's 32 consecutive
+// segments (lane j: segment first + j, its count word and its output offset
+// excl).  The records are expanded in passes: a pass takes consecutive
+// segments whose records fit in the 32 lanes (and no mask-format segment with
+// hits among them, so that the pass's positions are one output range); lane r
+// takes record r, a segmented warp scan of the records' hit counts places its
+// hits, which go to shared memory as offsets from the pass's first segment,
+// and the warp writes the pass's positions as consecutive 8-byte stores.
+__device__ __forceinline__ void emit_records(const StreamParams &P, uint64_t first, uint32_t word,
+                                             uint64_t excl, int64_t seg_pos0, uint16_t *stage,
+                                             int lane) {
+    const uint32_t c = word & kCountMask;
+    const uint32_t R = c ? (word >> 16) : 0u;  // records (0: none, or the mask format)
+    const uint32_t balR = __ballot_sync(kFull, R != 0u);
+    if (balR == 0u) return;
+    const uint32_t balM = __ballot_sync(kFull, c != 0u && R == 0u);
+    const uint32_t inclR = warp_incl_scan(R, lane);
+    const uint32_t exclR = inclR - R;
+    const uint64_t cincl = excl + c;  // output offset past this segment
+    uint32_t j0 = (uint32_t)(__ffs(balR) - 1);
+    for (;;) {
+        const uint32_t B = __shfl_sync(kFull, exclR, (int)j0);
+        uint32_t j1 = (uint32_t)__popc(__ballot_sync(kFull, inclR <= B + 32u));  // > j0
+        const uint32_t mafter = balM & ~((2u << j0) - 1u);
+        if (mafter) j1 = min(j1, (uint32_t)(__ffs(mafter) - 1));
+        const uint32_t TR = __shfl_sync(kFull, inclR, (int)(j1 - 1u)) - B;
+        const uint64_t E0 = __shfl_sync(kFull, excl, (int)j0);
+        const uint64_t E1 = __shfl_sync(kFull, cincl, (int)(j1 - 1u));
+        const uint32_t T = (uint32_t)(E1 - E0);  // hits of the pass, at most 32 x 16
+        // record g = B + lane: its segment j (lanes whose inclusive count <= g)
+        const uint32_t g = B + (uint32_t)lane;
+        uint32_t j = 0u;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const uint32_t v = __shfl_sync(kFull, inclR, (int)(j + (uint32_t)d - 1u));
+            if (v <= g) j += (uint32_t)d;
+        }
+        const bool act = (uint32_t)lane < TR;
+        j = act ? j : j0;
+        const uint32_t ej = __shfl_sync(kFull, exclR, (int)j);
+        const uint64_t oj = __shfl_sync(kFull, excl, (int)j);
+        uint32_t rec = 0u;
+        if (act)
+            rec = reinterpret_cast<const uint32_t *>(P.seg_mask + (first + j) * kSegChunks)[g - ej];
+        uint32_t mk = rec & 0xFFFFu;
+        const uint32_t cnt = __popc(mk);
+        const uint32_t incl = warp_incl_scan(cnt, lane);
+        const uint32_t f = ej - B;  // the segment's first lane in this pass
+        const uint32_t pre = __shfl_sync(kFull, incl, (int)(f > 0u ? f - 1u : 0u));
+        uint32_t k = (uint32_t)(oj - E0) + incl - cnt - (f > 0u ? pre : 0u);
+        const uint32_t off = (j - j0) * (uint32_t)(kSegChunks * 16) + (rec >> 16) * 16u;
+        while (mk) {
+            const uint32_t b = (uint32_t)(__ffs(mk) - 1);
+            mk &= mk - 1u;
+            stage[k++] = (uint16_t)(off + b);
+        }
+        __syncwarp();
+        const bool fits = E0 + T <= P.capacity;
+        if (lane == 0 && !fits) set_err(P.err, kErrCapacity);
+        const uint64_t base = (uint64_t)((int64_t)((first + j0) * kSegChunks * 16u) + seg_pos0);
+        uint64_t *dst = P.positions + E0;
+        if (fits) {
+            for (uint32_t q = (uint32_t)lane; q < T; q += 32u) dst[q] = base + stage[q];
+        } else {
+            for (uint32_t q = (uint32_t)lane; q < T; q += 32u)
+                if (E0 + q < P.capacity) dst[q] = base + stage[q];
+        }
+        __syncwarp();
+        if (j1 >= 32u) break;
+        const uint32_t rest = balR & ~((1u << j1) - 1u);
+        if (rest == 0u) break;
+        j0 = (uint32_t)(__ffs(rest) - 1);
+    }
+}
+
 // Ordered emission of the stages [st0, st1) from output offset base0:
 // batches of 256 segments, a block scan of their counts, and each warp emits
-// its segments with hits (their masks loaded ahead, see emit_list).
+// its segments with hits: those stored as masks one at a time (their masks
+// loaded ahead, see emit_list), those stored as chunk records in passes
+// (emit_records).
 __device__ __forceinline__ void emit_stages(const StreamParams &P, StreamEmitSmem &S, uint64_t st0,
                                             uint64_t st1, uint64_t base0, int w, int lane) {
     const int t = w * 32 + lane;
@@ -635,7 +749,8 @@ __device__ __forceinline__ void emit_stages(const StreamParams &P, StreamEmitSme
     const int64_t seg_pos0 = (int64_t)P.off - (int64_t)P.job.delta;
     for (uint64_t sb = seg0; sb < seg1; sb += kEmitThreads) {
         const uint64_t seg = sb + (uint64_t)t;
-        const uint32_t c = seg < seg1 ? P.seg_count[seg] : 0u;
+        const uint32_t word = seg < seg1 ? P.seg_count[seg] : 0u;
+        const uint32_t c = word & kCountMask;
         const uint32_t inc = warp_incl_scan(c, lane);
         if (lane == 31) S.scan_tmp[w] = inc;
         __syncthreads();
@@ -648,13 +763,15 @@ __device__ __forceinline__ void emit_stages(const StreamParams &P, StreamEmitSme
         }
         __syncthreads();
         const uint64_t excl = base + wbase + inc - c;
-        const uint32_t todo = __ballot_sync(kFull, c != 0u);
-        emit_list(todo, sb + (uint64_t)w * 32u, excl, P.seg_mask, lane,
+        const uint64_t first = sb + (uint64_t)w * 32u;
+        const uint32_t todo = __ballot_sync(kFull, c != 0u && (word >> 16) == 0u);
+        emit_list(todo, first, excl, P.seg_mask, lane,
                   [&](uint64_t sj, uint64_t ej, uint2 packed) {
                       const int64_t s0 = (int64_t)(sj * kSegChunks * 16u) + seg_pos0;
                       emit_segment(P.positions, P.capacity, P.err, s0, ej, packed,
                                    S.emit_stage[w], lane);
                   });
+        emit_records(P, first, word, excl, seg_pos0, S.emit_stage[w], lane);
         base += btotal;
     }
 }
@@ -699,8 +816,8 @@ __global__ void __launch_bounds__(stream::kThreadsStream, stream::kMaxBlocksPerS
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // S1: pattern preprocessing (block fingerprint table, Section 3.4)
-    if (V == V_BLOCK8) build_block_table(P.job.pat, S.table, S.pblk);
-    if (V == V_BLOCK8S) build_block_table16(P.job.pat, S.table, S.pblk);
+    if (V == V_BLOCK8) build_block_table(P.job.pat, S.table, S.pblk, 8);
+    if (V == V_BLOCK8S) build_block_table(P.job.pat, S.table, S.pblk, 16);
     // the previous kernel of the stream (a search's emission, or whatever
     // wrote the text) has finished before any global memory is touched
     grid_dep_wait();

@@ -14,37 +14,17 @@
 
 namespace epsm {
 
-// Pattern preprocessing for the block variant (Section 3.4, table L): the
-// fingerprints of the eight pattern blocks p[j..j+7], j = 0..7.  Must be
-// called by all threads of the block; ends with a barrier.
-__device__ __forceinline__ void build_block_table(const Pattern &pat, uint8_t *table,
-                                                  uint32_t *pblk) {
-    uint32_t *tw = reinterpret_cast<uint32_t *>(table);
-    for (int i = threadIdx.x; i < kHashSlots / 4; i += blockDim.x) tw[i] = 0u;
+// Pattern preprocessing for the block variants (Section 3.4, table L): the
+// fingerprints of the pattern blocks p[j..j+7], j < nb (8 for the plain block
+// variant; 16 for the strided one, whose inspected blocks lie at j = 0..15 of
+// an occurrence), marked in the bit table, and the blocks themselves in pblk
+// (2 * nb words).  Must be called by all threads of the block; ends with a
+// barrier.
+__device__ __forceinline__ void build_block_table(const Pattern &pat, uint32_t *table,
+                                                  uint32_t *pblk, int nb) {
+    for (int i = threadIdx.x; i < kTableWords; i += blockDim.x) table[i] = 0u;
     __syncthreads();
-    if (threadIdx.x < 8) {
-        int j = threadIdx.x;
-        int q = j >> 2;
-        uint32_t sh = 8u * (uint32_t)(j & 3);
-        uint32_t lo = __funnelshift_r(pat.w[q], pat.w[q + 1], sh);
-        uint32_t hi = __funnelshift_r(pat.w[q + 1], pat.w[q + 2], sh);
-        pblk[2 * j] = lo;
-        pblk[2 * j + 1] = hi;
-        table[block_hash(lo, hi)] = 1;
-    }
-    __syncthreads();
-}
-
-// The table of the strided block variant (Section 3.4 with the stride
-// sh of two blocks, 23 <= m <= 32): only every second aligned block is
-// inspected, so an occurrence's first inspected block lies at j = 0..15 and
-// the table holds the sixteen blocks p[j..j+7], j < 16 (pblk: 32 words).
-__device__ __forceinline__ void build_block_table16(const Pattern &pat, uint8_t *table,
-                                                    uint32_t *pblk) {
-    uint32_t *tw = reinterpret_cast<uint32_t *>(table);
-    for (int i = threadIdx.x; i < kHashSlots / 4; i += blockDim.x) tw[i] = 0u;
-    __syncthreads();
-    if (threadIdx.x < 16) {
+    if ((int)threadIdx.x < nb) {
         const int j = threadIdx.x;
         const int q = j >> 2;
         const uint32_t sh = 8u * (uint32_t)(j & 3);
@@ -52,7 +32,8 @@ __device__ __forceinline__ void build_block_table16(const Pattern &pat, uint8_t 
         const uint32_t hi = __funnelshift_r(pat.w[q + 1], pat.w[q + 2], sh);
         pblk[2 * j] = lo;
         pblk[2 * j + 1] = hi;
-        table[block_hash(lo, hi)] = 1;
+        const uint32_t h = block_hash(lo, hi, pat.kbits);
+        atomicOr(&table[h >> 5], 1u << (h & 31u));
     }
     __syncthreads();
 }
@@ -155,13 +136,11 @@ __device__ __noinline__ uint32_t exact_chunk_regs(const Pattern &pat, const uint
     return exact_starts16<8>(R, pat);
 }
 
-// Block variant, slow path: one of the chunk's two blocks hit a marked
-// fingerprint slot.  Compare the blocks with the pattern blocks p[j..j+7]; a
-// block match at j gives the candidate 8b - j, which is checked in full.
-// (Inlined: an out-of-line call in the filter loop costs it about 10%.)
-__device__ __forceinline__ uint32_t block_candidates(const SearchJob &J, const uint4 cur, int64_t p0,
-                                                  const uint32_t *pblk, uint32_t t0, uint32_t t1,
-                                                  const StagedText &T) {
+// Candidates of the block variant: the chunk's two blocks (those whose
+// fingerprint slot is marked: t0, t1) compared with the pattern blocks
+// p[j..j+7]; a block match at j gives the candidate 8b - j (Section 3.4).
+__device__ __forceinline__ uint32_t block_cands8(const uint4 cur, const uint32_t *pblk, uint32_t t0,
+                                                 uint32_t t1) {
     uint32_t cand = 0u;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -169,17 +148,139 @@ __device__ __forceinline__ uint32_t block_candidates(const SearchJob &J, const u
         if (t0 && cur.x == lo && cur.y == hi) cand |= 1u << (7 - j);
         if (t1 && cur.z == lo && cur.w == hi) cand |= 1u << (15 - j);
     }
-    if (kSoundness) cand = 0xFFFFu;  // soundness build: no block compare either
+    return kSoundness ? 0xFFFFu : cand;  // soundness build: no block compare either
+}
+
+// Candidates of the strided block variant: the chunk's first block against
+// p[j..j+7], j < 16, giving the candidate 16c - j (bit 15 - j).
+__device__ __forceinline__ uint32_t block_cands16(const uint4 cur, const uint32_t *pblk) {
+    uint32_t cand = 0u;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+        if (cur.x == pblk[2 * j] && cur.y == pblk[2 * j + 1]) cand |= 1u << (15 - j);
+    return kSoundness ? 0xFFFFu : cand;
+}
+
+// Full check of one lane's candidates (bit i <-> start p0 + i), in increasing
+// order; a candidate that lies q (the pattern's period) after a confirmed
+// occurrence needs only its last 8 bytes compared.
+__device__ __forceinline__ uint32_t verify_cands_serial(const SearchJob &J, int64_t p0, uint32_t cand,
+                                                        const StagedText &T) {
     uint32_t h = 0u;
+    int last = -64;
+    const int q = (int)J.pat.q;
     while (cand) {
-        int i = __ffs(cand) - 1;
+        const int i = __ffs(cand) - 1;
         cand &= cand - 1u;
-        int64_t P = p0 + i;
-        if (P >= (int64_t)J.delta && P <= J.pmax && verify_staged(J, P, T) &&
-            (T.mtail == 0u || verify_tail(J, P + 32, T.tail, T.mtail)))
+        const int64_t P = p0 + i;
+        if (P < (int64_t)J.delta || P > J.pmax) continue;
+        const bool ok = (q != 0 && i - last == q)
+                            ? tail8_ok(J, P, T)
+                            : verify_staged(J, P, T) &&
+                                  (T.mtail == 0u || verify_tail(J, P + 32, T.tail, T.mtail));
+        if (ok) {
             h |= 1u << i;
+            last = i;
+        }
     }
     return h;
+}
+
+// Position of the e-th set bit (e = 0, 1, ..) of a 16-bit mask that has more
+// than e set bits.
+__device__ __forceinline__ uint32_t nth_set_bit16(uint32_t x, uint32_t e) {
+    uint32_t pos = 0u, c = __popc(x & 0xFFu);
+    if (e >= c) { e -= c; x >>= 8; pos += 8u; }
+    c = __popc(x & 0xFu);
+    if (e >= c) { e -= c; x >>= 4; pos += 4u; }
+    c = __popc(x & 0x3u);
+    if (e >= c) { e -= c; x >>= 2; pos += 2u; }
+    if (e >= (x & 1u)) pos += 1u;
+    return pos;
+}
+
+// Warp-cooperative full check of the lanes' candidates (bit i of `cand` <->
+// start p0 + i; a whole warp calls it).  The warp's candidates are numbered
+// in lane order and each round the 32 lanes check 32 of them, so that a lane
+// with many candidates (a run of one byte, a periodic stretch of text) does
+// not hold the warp for up to 16 serial checks.  Each check's result goes back
+// to the candidate's lane by an OR-reduction over the lanes that checked that
+// lane's candidates.  Returns the lane's hits.
+__device__ __noinline__ uint32_t coop_verify(const SearchJob &J, int64_t p0, uint32_t cand,
+                                             const uint8_t *buf, int64_t sbase, uint32_t inside,
+                                             const uint8_t *tail, uint32_t mtail) {
+    StagedText T;
+    T.buf = buf;
+    T.sbase = sbase;
+    T.span = (uint32_t)((1024 + 1) * 16);
+    T.inside = inside;
+    T.tail = tail;
+    T.mtail = mtail;
+    const int lane = (int)(threadIdx.x & 31u);
+    const uint32_t c = __popc(cand);
+    const uint32_t incl = warp_incl_scan(c, lane);
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    const uint32_t excl = incl - c;
+    uint32_t h = 0u;
+    for (uint32_t base = 0; base < total; base += 32u) {
+        const uint32_t k = base + (uint32_t)lane;
+        // owner of candidate k: the number of lanes whose inclusive count is <= k
+        uint32_t L = 0u;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            const uint32_t v = __shfl_sync(kFull, incl, (int)(L + (uint32_t)d - 1u));
+            if (v <= k) L += (uint32_t)d;
+        }
+        const bool act = k < total;
+        const int src = act ? (int)L : lane;
+        const uint32_t cL = __shfl_sync(kFull, cand, src);
+        const uint32_t eL = __shfl_sync(kFull, excl, src);
+        const int64_t pL = __shfl_sync(kFull, p0, src);
+        uint32_t bitv = 0u;
+        if (act) {
+            const uint32_t bit = nth_set_bit16(cL, k - eL);
+            const int64_t P = pL + (int64_t)bit;
+            if (P >= (int64_t)J.delta && P <= J.pmax && verify_staged(J, P, T) &&
+                (T.mtail == 0u || verify_tail(J, P + 32, T.tail, T.mtail)))
+                bitv = 1u << bit;
+        }
+        // OR of the results over the lanes that checked the same owner's
+        // candidates (inactive lanes form their own group)
+        const uint32_t grp = __match_any_sync(kFull, act ? L : 32u + (uint32_t)lane);
+        const uint32_t orv = __reduce_or_sync(grp, bitv);
+        // the owner takes it from the first lane that checked its candidates
+        const uint32_t lo = excl > base ? excl : base;
+        const uint32_t hi = incl < base + 32u ? incl : base + 32u;
+        const uint32_t got = __shfl_sync(kFull, orv, lo < hi ? (int)(lo - base) : lane);
+        if (lo < hi) h |= got;
+    }
+    return h;
+}
+
+// Slow path of the block variants, out of line and reached by the whole warp
+// when some lane's block hit a marked fingerprint slot (t0: the chunk's first
+// block, t1: its second; the strided variant inspects the first only): the
+// lanes' candidates from the block compare, checked cooperatively when some
+// lane has more than a few, else each lane its own (usually one).
+constexpr int kCoopMin = 2;
+template <int V>
+__device__ __noinline__ uint32_t block_slow(const SearchJob &J, const uint4 cur, int64_t p0,
+                                            const uint32_t *pblk, uint32_t t0, uint32_t t1,
+                                            const uint8_t *buf, int64_t sbase, uint32_t inside,
+                                            const uint8_t *tail, uint32_t mtail) {
+    const uint32_t cand = V == V_BLOCK8S ? (t0 ? block_cands16(cur, pblk) : 0u)
+                                         : ((t0 | t1) ? block_cands8(cur, pblk, t0, t1) : 0u);
+    if (__any_sync(kFull, __popc(cand) > kCoopMin))
+        return coop_verify(J, p0, cand, buf, sbase, inside, tail, mtail);
+    if (!cand) return 0u;
+    StagedText T;
+    T.buf = buf;
+    T.sbase = sbase;
+    T.span = (uint32_t)((1024 + 1) * 16);
+    T.inside = inside;
+    T.tail = tail;
+    T.mtail = mtail;
+    return verify_cands_serial(J, p0, cand, T);
 }
 
 // Full in-register check of the start at byte 4K + b of the chunk (RR: the
@@ -245,26 +346,6 @@ __device__ __forceinline__ uint32_t even_bits(uint32_t z) {
     return (z | (z >> 8)) & 0x0000FFFFu;
 }
 
-// Strided block variant, slow path: the chunk's first block hit a marked slot;
-// a match with p[j..j+7] (j < 16) gives the candidate 16c - j, bit 15 - j of
-// the chunk's starts 16c - 15 .. 16c, checked in full.
-__device__ __forceinline__ uint32_t block16_candidates(const SearchJob &J, const uint4 cur, int64_t p0,
-                                                       const uint32_t *pblk, const StagedText &T) {
-    uint32_t cand = 0u;
-#pragma unroll
-    for (int j = 0; j < 16; ++j)
-        if (cur.x == pblk[2 * j] && cur.y == pblk[2 * j + 1]) cand |= 1u << (15 - j);
-    if (kSoundness) cand = 0xFFFFu;
-    uint32_t h = 0u;
-    while (cand) {
-        const int i = __ffs(cand) - 1;
-        cand &= cand - 1u;
-        const int64_t P = p0 + i;
-        if (P >= (int64_t)J.delta && P <= J.pmax && verify_staged(J, P, T)) h |= 1u << i;
-    }
-    return h;
-}
-
 // 4-byte block variant, slow path: a word k of the chunk (k = 0..3) or the
 // next chunk's first word (k = 4) equals a pattern block p[j..j+3] (q[j]); the
 // match gives the candidate start 4k - j when it lies in the chunk
@@ -308,7 +389,7 @@ __device__ __forceinline__ bool block4_any(const uint4 cur, uint32_t n0, uint32_
 template <int V, int MP>
 __device__ __forceinline__ uint32_t chunk_hits(const SearchJob &J, const uint4 cur,
                                                const uint4 nsrc, int64_t p0,
-                                               const BcastWords &B, const uint8_t *table,
+                                               const BcastWords &B, const uint32_t *table,
                                                const uint32_t *pblk, int lane,
                                                const StagedText &T) {
     const int src = (lane + 1) & 31;
@@ -425,20 +506,20 @@ __device__ __forceinline__ uint32_t chunk_hits(const SearchJob &J, const uint4 c
         // Section 3.4 (EPSMc) with the block stride sh of two blocks: only
         // the chunk's first block is fingerprinted (half the hashing and
         // lookups of the plain block variant); starts 16c - 15 .. 16c.
-        const uint32_t t0 = kSoundness ? 1u : table[block_hash(cur.x, cur.y)];
-        if (t0) return block16_candidates(J, cur, p0, pblk, T);
-        return 0u;
+        const uint32_t t0 = kSoundness ? 1u : table_bit(table, block_hash(cur.x, cur.y, pat.kbits));
+        if (!__any_sync(kFull, t0 != 0u)) return 0u;
+        return block_slow<V_BLOCK8S>(J, cur, p0, pblk, t0, 0u, T.buf, T.sbase, T.inside, T.tail,
+                                     T.mtail);
     } else {
         // Section 3.4 (EPSMc) on aligned 8-byte blocks: fingerprint each block,
         // and where the slot is marked compare the block with the pattern
         // blocks p[j..j+7]; a block match at j gives the candidate 8b - j,
         // which is then checked in full.
-        const uint32_t h0 = block_hash(cur.x, cur.y);
-        const uint32_t h1 = block_hash(cur.z, cur.w);
-        const uint32_t t0 = kSoundness ? 1u : table[h0];  // soundness build: every block marked
-        const uint32_t t1 = kSoundness ? 1u : table[h1];
-        if (t0 | t1) return block_candidates(J, cur, p0, pblk, t0, t1, T);
-        return 0u;
+        const uint32_t t0 = kSoundness ? 1u : table_bit(table, block_hash(cur.x, cur.y, pat.kbits));
+        const uint32_t t1 = kSoundness ? 1u : table_bit(table, block_hash(cur.z, cur.w, pat.kbits));
+        if (!__any_sync(kFull, (t0 | t1) != 0u)) return 0u;
+        return block_slow<V_BLOCK8>(J, cur, p0, pblk, t0, t1, T.buf, T.sbase, T.inside, T.tail,
+                                    T.mtail);
     }
 }
 

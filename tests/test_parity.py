@@ -6,6 +6,7 @@ import pytest
 
 import gen
 import oracle
+from tests._texts import periodic_runs_text
 
 pytestmark = pytest.mark.gpu
 
@@ -78,6 +79,20 @@ def test_dense_runs_every_alignment(ctx, torch, variant):
     for m in VARIANTS[variant]:
         for off in range(16):
             _check(ctx, torch, host, b"a" * m, variant, offset=off)
+
+
+@pytest.mark.parametrize("variant", sorted(VARIANTS))
+def test_periodic_patterns_in_periodic_runs(ctx, torch, variant):
+    """Periodic patterns (period 1..10) in runs of the same periodic strings:
+    dense candidates, each run's occurrences q apart (the block variants
+    confirm those from the pattern's last 8 bytes after a full check)."""
+    n = 6 * TILE + 515
+    host, units = periodic_runs_text(n, 40 + variant)
+    for m in VARIANTS[variant]:
+        for u in units:
+            p = (u * (m // len(u) + 2))[:m]
+            for off in (0, 7):
+                _check(ctx, torch, host, p, variant, offset=off)
 
 
 @pytest.mark.parametrize("variant", sorted(VARIANTS))

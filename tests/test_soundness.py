@@ -10,6 +10,7 @@ import pytest
 
 import gen
 import oracle
+from tests._texts import periodic_runs_text
 
 pytestmark = pytest.mark.gpu
 
@@ -63,6 +64,22 @@ def test_verification_alone_is_exact(sound, torch, kind):
                     want = oracle.search(ref, p)
                     c, got = _search(sound, torch, dev, n - off, p, v, want.size + 8)
                     assert c == want.size and np.array_equal(got, want), (kind, v, m, off)
+
+
+def test_verification_alone_periodic(sound, torch):
+    """Periodic patterns in runs of periodic strings: with every start a
+    candidate, the block variants' shortcut for the start one period after a
+    confirmed occurrence must stay exact."""
+    n = 4 * 16384 + 99
+    host, units = periodic_runs_text(n, 77)
+    dev = torch.from_numpy(host).cuda()
+    for v in (4, 8):
+        for m in (VARIANTS[v][0], 24, 32):
+            for u in units:
+                p = (u * (m // len(u) + 2))[:m]
+                want = oracle.search(host, p)
+                c, got = _search(sound, torch, dev, n, p, v, want.size + 8)
+                assert c == want.size and np.array_equal(got, want), (v, m, u)
 
 
 def test_verification_alone_long_patterns(sound, torch):
