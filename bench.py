@@ -411,6 +411,37 @@ def run_sample(args):
     return 0 if st == 0 else 1
 
 
+# alphabet class of each text kind (rows of the tuning table a context uses)
+KIND_CLASS = {"dna": "dna", "dna_runs": "dna", "protein": "protein", "nl64": "text",
+              "markov96": "text"}
+
+
+class Contexts:
+    """One library context per alphabet class of the workload's texts, each
+    with its class's rows of the tuning table."""
+
+    def __init__(self, epsm, device, kinds):
+        self.by_class = {c: epsm.Context(device, text_class=c)
+                         for c in sorted({KIND_CLASS[k] for k in kinds})}
+
+    def __getitem__(self, kind):
+        return self.by_class[KIND_CLASS[kind]]
+
+    @property
+    def launch_count(self):
+        return sum(c.launch_count for c in self.by_class.values())
+
+    def sync(self):
+        st = 0
+        for c in self.by_class.values():
+            st = st or c.sync()
+        return st
+
+    def close(self):
+        for c in self.by_class.values():
+            c.close()
+
+
 def make_texts(torch, dev, kinds, n, stream):
     import gen
     texts = {}
@@ -431,7 +462,7 @@ def measure(ctx, torch, texts, pats, steps, warmup, stream, dist=None, clocks_in
     counts = torch.zeros(nsearch, dtype=torch.int64, device=stream.device)
     # output room: the densest search of the workload (from a count-only pass)
     for i, (kind, m, _, p) in enumerate(pats):
-        ctx.search_async(texts[kind], p, counts, 0, counts[i:i + 1], stream=stream)
+        ctx[kind].search_async(texts[kind], p, counts, 0, counts[i:i + 1], stream=stream)
     torch.cuda.synchronize()
     if ctx.sync() != 0:
         raise SystemExit("device status after the count pass")
@@ -441,7 +472,7 @@ def measure(ctx, torch, texts, pats, steps, warmup, stream, dist=None, clocks_in
 
     def step():
         for i, (kind, m, _, p) in enumerate(pats):
-            ctx.search_async(texts[kind], p, out, cap, counts[i:i + 1], stream=stream)
+            ctx[kind].search_async(texts[kind], p, out, cap, counts[i:i + 1], stream=stream)
 
     for _ in range(warmup):
         step()
@@ -482,7 +513,7 @@ def measure(ctx, torch, texts, pats, steps, warmup, stream, dist=None, clocks_in
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(nsearch + 1)]
     evs[0].record(stream)
     for i, (kind, m, _, p) in enumerate(pats):
-        ctx.search_async(texts[kind], p, out, cap, counts[i:i + 1], stream=stream)
+        ctx[kind].search_async(texts[kind], p, out, cap, counts[i:i + 1], stream=stream)
         evs[i + 1].record(stream)
     torch.cuda.synchronize()
     per = [evs[i].elapsed_time(evs[i + 1]) for i in range(nsearch)]
@@ -561,7 +592,7 @@ def run_e2e(ctx, torch, texts, pats, steps, warmup, occ, dist=None):
     def step():
         d2h = 0
         for k, group in calls:
-            st, offs = epsm_search_host(ctx.handle, hosts[k], group, pos_host)
+            st, offs = epsm_search_host(ctx[k].handle, hosts[k], group, pos_host)
             if st != 0:
                 raise SystemExit(f"epsm_search_host status {st}")
             d2h += int(offs[-1]) * 8
@@ -747,7 +778,7 @@ def main():
     else:
         torch.cuda.set_device(0)
     dev = torch.device(f"cuda:{local if world > 1 else 0}")
-    ctx = epsm.Context(dev.index)
+    ctx = Contexts(epsm, dev.index, SCAN_KINDS + KINDS)
     stream = torch.cuda.current_stream()
     peak, peak_kind = measured_peaks()
 
@@ -801,7 +832,7 @@ def main():
                  "clocks": sres["clocks"]}
     batched = None
     if not args.no_batch:
-        batched = run_batched(ctx, torch, args.batch_pairs)
+        batched = run_batched(ctx["dna"], torch, args.batch_pairs)
     served = None
     if not args.no_serve and world == 1:
         torch.cuda.empty_cache()

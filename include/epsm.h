@@ -162,12 +162,40 @@ epsm_status epsm_search_batch(epsm_ctx *ctx, uint32_t npairs,
  * the context (grown on demand).  If the total exceeds `capacity`, the first
  * `capacity` positions are copied, the offsets are the true ones, and the call
  * returns EPSM_ERR_CAPACITY. */
-/* Variant the context uses for pattern length m under EPSM_VARIANT_AUTO. */
+/* Variant the context uses for pattern length m under EPSM_VARIANT_AUTO on the
+ * longest texts (the last bucket of the tuning table below). */
 int epsm_variant_for(epsm_ctx *ctx, uint32_t m);
 
-/* Override the automatic variant for pattern length m (1..32); `variant` must
- * cover m.  Used by the autotuner to install its table. */
+/* Override the automatic variant for pattern length m (1..32) in every bucket
+ * of the tuning table; `variant` must cover m. */
 epsm_status epsm_set_variant(epsm_ctx *ctx, uint32_t m, int variant);
+
+/* Tuning table of a context.  For each text-length bucket and pattern length
+ * m (1..32; longer patterns use the m = 32 entry's shape and width) the table
+ * holds:
+ *   variant  the kernel variant EPSM_VARIANT_AUTO picks (must cover m);
+ *   shape    the filter kernel's launch shape: 0 = a 6-stage ring of 16 KiB
+ *            stages with 2 blocks per SM, 1 = a 4-stage ring with 3 blocks per
+ *            SM (the default);
+ *   kbits    the width k of the block variants' fingerprint table, 2^k bits
+ *            (Section 3.4 takes k = 11; default 14; EPSM_KBITS_MIN..MAX).
+ * Buckets: n < EPSM_BUCKET1_MIN, n < EPSM_BUCKET2_MIN, and larger texts.
+ * The results do not depend on the table, only the speed does. */
+#define EPSM_TEXT_BUCKETS 3
+#define EPSM_BUCKET1_MIN (16ull << 20)
+#define EPSM_BUCKET2_MIN (512ull << 20)
+#define EPSM_KBITS_MIN 8u
+#define EPSM_KBITS_MAX 14u
+
+/* Sets the entry of one bucket (0..2) or of all buckets (bucket = -1) for m:
+ * variant EPSM_VARIANT_AUTO, shape -1 or kbits 0 keep the current value.
+ * EPSM_ERR_ARG for a value out of range or a variant that does not cover m. */
+epsm_status epsm_set_tuning(epsm_ctx *ctx, int bucket, uint32_t m, int variant, int shape,
+                            uint32_t kbits);
+
+/* Reads the entry of bucket (0..2) for m; NULL outputs are skipped. */
+epsm_status epsm_get_tuning(epsm_ctx *ctx, int bucket, uint32_t m, int *variant, int *shape,
+                            uint32_t *kbits);
 
 /* Number of kernel launches the context has issued (all entry points). */
 uint64_t epsm_launch_count(epsm_ctx *ctx);

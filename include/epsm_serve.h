@@ -39,7 +39,9 @@ typedef struct epsm_server_config {
     uint32_t inflight;       /* launches on the device at once, 1..4 (0: 2) */
     uint32_t per_query;      /* 1: one single-search launch per query instead of batches
                                 (the plain per-query path, for comparison) */
-    uint32_t pad;
+    uint32_t small_batch;    /* a batch of at most this many distinct queries runs as
+                                single searches, whose fixed cost is lower than a
+                                batched launch's (0: 3; at most 8) */
     uint64_t upload_budget;  /* device bytes uploaded texts may hold (0: no budget beyond
                                 free memory minus `reserve`) */
     uint64_t reserve;        /* device bytes admission leaves free (0: 4 GiB) */
@@ -120,6 +122,23 @@ typedef struct epsm_server_stats {
 } epsm_server_stats;
 
 epsm_status epsm_server_stats_get(epsm_server *srv, epsm_server_stats *out);
+
+/* Host-side fault injection (for testing the engine's failure handling; no
+ * GPU fault is involved).  Arms `count` more failures of one kind, each of
+ * which fires once, at the next point of that kind:
+ *   EPSM_FAULT_ALLOC   obtaining an output buffer for a batch fails: every
+ *                      query of that batch completes with EPSM_ERR_NOMEM;
+ *   EPSM_FAULT_ADMIT   admission refuses an upload: the upload completes with
+ *                      EPSM_ERR_NOMEM;
+ *   EPSM_FAULT_UPLOAD  an upload's copy to the device fails: the upload
+ *                      completes with EPSM_ERR_CUDA and its memory is freed.
+ * The engine keeps serving afterwards.  The environment variable EPSM_FAULT,
+ * read when an engine is created, arms the same (e.g. "alloc:2,upload:1").
+ * EPSM_ERR_ARG for a NULL engine or an unknown kind. */
+#define EPSM_FAULT_ALLOC 0
+#define EPSM_FAULT_ADMIT 1
+#define EPSM_FAULT_UPLOAD 2
+epsm_status epsm_server_inject_fault(epsm_server *srv, int kind, uint32_t count);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,7 @@ from ._native import (MAX_M, MAX_M_LONG, STATIC_MAX_TEXT, STATUS_NAMES, VARIANT_
 __all__ = ["Context", "EpsmError", "Server", "epsm_create", "epsm_destroy", "epsm_status_str",
            "epsm_search", "epsm_search_async", "epsm_search_variant", "epsm_sync",
            "epsm_search_batch", "epsm_search_host", "epsm_variant_for", "epsm_set_variant",
-           "epsm_launch_count", "epsm_search_static", "epsm_wait_probe", "STATIC_MAX_TEXT", "MAX_M", "MAX_M_LONG", "VARIANT_AUTO", "VARIANT_DIRECT", "VARIANT_PREFIX4",
+           "epsm_launch_count", "epsm_search_static", "epsm_set_tuning", "epsm_get_tuning", "epsm_wait_probe", "STATIC_MAX_TEXT", "MAX_M", "MAX_M_LONG", "VARIANT_AUTO", "VARIANT_DIRECT", "VARIANT_PREFIX4",
            "VARIANT_PREFIX8", "VARIANT_BLOCK8", "VARIANT_BLOCK4", "VARIANT_CODE2", "VARIANT_ADAPT", "VARIANT_BLOCK8S",
            "VARIANT_NAMES"]
 
@@ -142,6 +142,18 @@ def epsm_set_variant(ctx: int, m: int, variant: int) -> int:
     return _lib.epsm_set_variant(ctx, m, variant)
 
 
+def epsm_set_tuning(ctx: int, bucket: int, m: int, variant: int = 0, shape: int = -1,
+                    kbits: int = 0) -> int:
+    return _lib.epsm_set_tuning(ctx, bucket, m, variant, shape, kbits)
+
+
+def epsm_get_tuning(ctx: int, bucket: int, m: int):
+    """Returns (status, variant, shape, kbits)."""
+    v, sh, kb = ctypes.c_int(), ctypes.c_int(), ctypes.c_uint32()
+    st = _lib.epsm_get_tuning(ctx, bucket, m, ctypes.byref(v), ctypes.byref(sh), ctypes.byref(kb))
+    return st, v.value, sh.value, kb.value
+
+
 def epsm_launch_count(ctx: int) -> int:
     return _lib.epsm_launch_count(ctx)
 
@@ -161,10 +173,12 @@ def epsm_search_static(text: int, n: int, pattern: bytes, m: int, positions: int
 class Context:
     """One library context on one CUDA device (not thread-safe)."""
 
-    def __init__(self, device: int = 0, tuning: str | None = "default"):
-        """``tuning``: "default" installs the measured variant table shipped
+    def __init__(self, device: int = 0, tuning: str | None = "default", text_class: str = "mixed"):
+        """``tuning``: "default" installs the measured tuning table shipped
         next to this file (if present); a path installs that table; None keeps
-        the library's built-in choice."""
+        the library's built-in choice.  ``text_class`` picks the table's rows
+        for an alphabet class ("dna", "protein", "text") or the rows best over
+        all classes ("mixed")."""
         import torch
         self._torch = torch
         self.device = device
@@ -174,7 +188,7 @@ class Context:
             from . import autotune
             table = autotune.load() if tuning == "default" else autotune.load(tuning)
             if table is not None:
-                autotune.apply(self, table)
+                autotune.apply(self, table, text_class)
 
     def close(self):
         if self.handle:
@@ -272,6 +286,16 @@ class Context:
         if st not in (0, _native.ERR_CAPACITY):
             self._check(st, "epsm_search_host")
         return offs, pos
+
+    def set_tuning(self, bucket: int, m: int, variant: int = 0, shape: int = -1, kbits: int = 0):
+        """One entry of the tuning table (bucket -1: every text-length bucket)."""
+        self._check(epsm_set_tuning(self.handle, bucket, m, variant, shape, kbits), "epsm_set_tuning")
+
+    def get_tuning(self, bucket: int, m: int):
+        """(variant, shape, kbits) of one entry of the tuning table."""
+        st, v, sh, kb = epsm_get_tuning(self.handle, bucket, m)
+        self._check(st, "epsm_get_tuning")
+        return v, sh, kb
 
     def variant_for(self, m: int) -> int:
         return epsm_variant_for(self.handle, m)

@@ -24,10 +24,21 @@ EXPORTS = ["epsm_create", "epsm_destroy", "epsm_status_str", "epsm_last_error",
            "epsm_search", "epsm_search_async", "epsm_search_variant", "epsm_sync",
            "epsm_search_batch", "epsm_search_host", "epsm_variant_for", "epsm_set_variant",
            "epsm_launch_count", "epsm_search_static", "epsm_batch_uses_graph",
+           "epsm_set_tuning", "epsm_get_tuning",
            "epsm_server_create", "epsm_server_destroy", "epsm_server_add_corpus",
            "epsm_server_upload", "epsm_server_submit", "epsm_server_poll", "epsm_server_read",
-           "epsm_server_release", "epsm_server_replay", "epsm_server_stats_get"]
+           "epsm_server_release", "epsm_server_replay", "epsm_server_stats_get",
+           "epsm_server_inject_fault"]
 STATIC_MAX_TEXT = 64 << 20
+TEXT_BUCKETS = 3
+BUCKET_MIN = (0, 16 << 20, 512 << 20)   # first text length of each tuning-table bucket
+KBITS_MIN, KBITS_MAX = 8, 14
+SHAPES = 2
+
+
+def text_bucket(n: int) -> int:
+    """Bucket of the tuning table a text of n bytes falls in."""
+    return 0 if n < BUCKET_MIN[1] else (1 if n < BUCKET_MIN[2] else 2)
 
 
 def lib_path() -> str:
@@ -73,6 +84,11 @@ def load(path: str | None = None):
     lib.epsm_variant_for.restype = i32
     lib.epsm_set_variant.argtypes = [vp, u32, i32]
     lib.epsm_set_variant.restype = st
+    lib.epsm_set_tuning.argtypes = [vp, i32, u32, i32, i32, u32]
+    lib.epsm_set_tuning.restype = st
+    lib.epsm_get_tuning.argtypes = [vp, i32, u32, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                    ctypes.POINTER(u32)]
+    lib.epsm_get_tuning.restype = st
     lib.epsm_launch_count.argtypes = [vp]
     lib.epsm_launch_count.restype = u64
     lib.epsm_batch_uses_graph.argtypes = [vp]
@@ -100,6 +116,8 @@ def load(path: str | None = None):
     lib.epsm_server_replay.restype = st
     lib.epsm_server_stats_get.argtypes = [vp, vp]
     lib.epsm_server_stats_get.restype = st
+    lib.epsm_server_inject_fault.argtypes = [vp, i32, u32]
+    lib.epsm_server_inject_fault.restype = st
     if path is None:
         _lib = lib
     return lib

@@ -186,6 +186,17 @@ size_t batch_stage_bytes(uint32_t cap) {
 
 }  // namespace
 
+struct Tune {
+    int variant;
+    int shape;
+    uint32_t kbits;
+};
+
+// Text-length bucket of the tuning table (boundaries in include/epsm.h).
+int text_bucket(uint64_t n) {
+    return n < EPSM_BUCKET1_MIN ? 0 : n < EPSM_BUCKET2_MIN ? 1 : 2;
+}
+
 struct epsm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -195,7 +206,9 @@ struct epsm_ctx {
     cudaEvent_t ev = nullptr;
     cudaStream_t last_stream = nullptr;
     bool have_ev = false;
-    int variant[EPSM_MAX_M + 1];
+    // tuning table: per text-length bucket and pattern length, the variant,
+    // the filter kernel's launch shape and the block fingerprint width
+    Tune tune[EPSM_TEXT_BUCKETS][EPSM_MAX_M + 1];
     uint64_t launches = 0;
     char errbuf[256];
     // batched launch
@@ -283,12 +296,12 @@ int stream_emit_grid(int sms) {
 
 // A single search: the streaming filter kernel (epsm_stream.cuh; up to two
 // blocks per SM), then, when positions are wanted, the emission kernel.
-template <int V, int MP>
+template <int V, int MP, int SH>
 cudaError_t launch_stream_t(int sms, stream::StreamParams &p, cudaStream_t s) {
     static std::atomic<int> cache[kMaxDevices];
-    const size_t smem = sizeof(stream::StreamSmem);
-    const int per_sm = blocks_per_sm(stream_kernel<V, MP>, stream::kThreadsStream, smem,
-                                     stream::kMaxBlocksPerSm, cache);
+    const size_t smem = sizeof(stream::StreamSmem<stream::Shape<SH>::stages>);
+    const int per_sm = blocks_per_sm(stream_kernel<V, MP, SH>, stream::kThreadsStream, smem,
+                                     stream::Shape<SH>::blocks, cache);
     if (per_sm == 0) return cudaErrorInvalidDevice;
     uint64_t grid = std::min<uint64_t>(std::max<uint64_t>(p.nstages, 1u), (uint64_t)sms * per_sm);
     grid = std::min<uint64_t>(grid, stream::kMaxBlocks);
@@ -311,7 +324,7 @@ cudaError_t launch_stream_t(int sms, stream::StreamParams &p, cudaStream_t s) {
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, stream_kernel<V, MP>, p);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, stream_kernel<V, MP, SH>, p);
     if (e != cudaSuccess || !p.emit) return e;
     const int eg = stream_emit_grid(sms);
     if (eg == 0) return cudaErrorUnknown;
@@ -321,24 +334,31 @@ cudaError_t launch_stream_t(int sms, stream::StreamParams &p, cudaStream_t s) {
     return cudaLaunchKernelEx(&cfg, stream_emit_kernel, p);
 }
 
-cudaError_t launch_stream(int sms, int v, uint32_t m, stream::StreamParams &p,
-                          cudaStream_t s) {
+template <int SH>
+cudaError_t launch_stream_shape(int sms, int v, uint32_t m, stream::StreamParams &p, cudaStream_t s) {
     switch (v) {
         case V_DIRECT:
             switch (m) {
-                case 1: return launch_stream_t<V_DIRECT, 1>(sms, p, s);
-                case 2: return launch_stream_t<V_DIRECT, 2>(sms, p, s);
-                case 3: return launch_stream_t<V_DIRECT, 3>(sms, p, s);
-                default: return launch_stream_t<V_DIRECT, 4>(sms, p, s);
+                case 1: return launch_stream_t<V_DIRECT, 1, SH>(sms, p, s);
+                case 2: return launch_stream_t<V_DIRECT, 2, SH>(sms, p, s);
+                case 3: return launch_stream_t<V_DIRECT, 3, SH>(sms, p, s);
+                default: return launch_stream_t<V_DIRECT, 4, SH>(sms, p, s);
             }
-        case V_PREFIX4: return launch_stream_t<V_PREFIX4, 4>(sms, p, s);
-        case V_PREFIX8: return launch_stream_t<V_PREFIX8, 8>(sms, p, s);
-        case V_BLOCK4: return launch_stream_t<V_BLOCK4, 4>(sms, p, s);
-        case V_CODE2: return launch_stream_t<V_CODE2, 4>(sms, p, s);
-        case V_ADAPT: return launch_stream_t<V_ADAPT, 4>(sms, p, s);
-        case V_BLOCK8S: return launch_stream_t<V_BLOCK8S, 8>(sms, p, s);
-        default: return launch_stream_t<V_BLOCK8, 8>(sms, p, s);
+        case V_PREFIX4: return launch_stream_t<V_PREFIX4, 4, SH>(sms, p, s);
+        case V_PREFIX8: return launch_stream_t<V_PREFIX8, 8, SH>(sms, p, s);
+        case V_BLOCK4: return launch_stream_t<V_BLOCK4, 4, SH>(sms, p, s);
+        case V_CODE2: return launch_stream_t<V_CODE2, 4, SH>(sms, p, s);
+        case V_ADAPT: return launch_stream_t<V_ADAPT, 4, SH>(sms, p, s);
+        case V_BLOCK8S: return launch_stream_t<V_BLOCK8S, 8, SH>(sms, p, s);
+        default: return launch_stream_t<V_BLOCK8, 8, SH>(sms, p, s);
     }
+}
+
+// A single search with the filter kernel's launch shape `shape` (0: 6-stage
+// ring, 2 blocks per SM; 1: 4-stage ring, 3 blocks per SM).
+cudaError_t launch_stream(int sms, int v, uint32_t m, int shape, stream::StreamParams &p,
+                          cudaStream_t s) {
+    return shape == 0 ? launch_stream_shape<0>(sms, v, m, p, s) : launch_stream_shape<1>(sms, v, m, p, s);
 }
 
 // Stages of 16 KiB needed for a job: stage k covers starts [16K*k + OFF, 16K*(k+1) + OFF).
@@ -359,7 +379,8 @@ epsm_status search_async_impl(epsm_ctx *c, int variant, const uint8_t *text, uin
     // a long pattern: the 8-byte block filter and check on its first 32
     // bytes, then the rest of the pattern checked at each candidate
     const bool longp = m > EPSM_MAX_M;
-    int v = variant == EPSM_VARIANT_AUTO ? (longp ? V_BLOCK8 : c->variant[m]) : variant;
+    const Tune &T = c->tune[text_bucket(n)][longp ? EPSM_MAX_M : m];
+    int v = variant == EPSM_VARIANT_AUTO ? (longp ? V_BLOCK8 : T.variant) : variant;
     if (!(longp ? v == V_BLOCK8 : variant_covers(v, m))) return EPSM_ERR_ARG;
     cudaStream_t s = pick_stream(c, stream);
     epsm_status st = order_after_previous(c, s);
@@ -371,6 +392,7 @@ epsm_status search_async_impl(epsm_ctx *c, int variant, const uint8_t *text, uin
     stream::StreamParams p;
     memset(&p, 0, sizeof(p));
     p.job = make_job(text, n, pack_pattern(pattern, longp ? EPSM_MAX_M : m));
+    p.job.pat.kbits = T.kbits;
     if (longp) {
         p.job.pmax = (int64_t)(p.job.delta + n) - (int64_t)m;
         p.job.pat.q = 0;  // (the period shortcut covers patterns of at most 32 bytes)
@@ -402,7 +424,7 @@ epsm_status search_async_impl(epsm_ctx *c, int variant, const uint8_t *text, uin
     p.range_total = c->range_total;
     p.err = &c->misc->err;
     p.misc = c->misc;
-    CK(launch_stream(c->sms, v, m, p, s));
+    CK(launch_stream(c->sms, v, m, T.shape, p, s));
     c->launches += p.emit ? 2 : 1;  // filter kernel (+ emission kernel)
     return mark_done(c, s);
 }
@@ -440,7 +462,7 @@ void free_batch(BatchRes &R) {
 int batch_grid(int sms) {
     static std::atomic<int> cache[kMaxDevices];
     const int per_sm = blocks_per_sm(group_kernel, stream::kThreadsStream, sizeof(group::Smem),
-                                     stream::kMaxBlocksPerSm, cache);
+                                     group::kGroupBlocksPerSm, cache);
     return (int)std::min<uint64_t>((uint64_t)sms * per_sm, stream::kMaxBlocks);
 }
 
@@ -700,11 +722,13 @@ epsm_status batch_submit(epsm_ctx *c, uint32_t npairs, const uint8_t *const *tex
         JobDesc D;
         memset(&D, 0, sizeof(D));
         D.job = make_job(texts[i], ns[i], pack_pattern(patterns[i], m));
+        D.job.pat.kbits = c->tune[text_bucket(ns[i])][m].kbits;
         // shared patterns are numbered like the window variants (offset 0);
         // short patterns of a shared text run the direct compare
         // (the strided block variant is single-search only: its batch form is
         // the plain block variant)
-        const int vt = c->variant[m] == V_BLOCK8S ? V_BLOCK8 : c->variant[m];
+        const Tune &T = c->tune[text_bucket(ns[i])][m];
+        const int vt = T.variant == V_BLOCK8S ? V_BLOCK8 : T.variant;
         D.variant = (uint32_t)(kstr[i] ? V_PREFIX4 : multi[i] ? V_DIRECT : vt);
         const uint64_t nst = stages_for(D.job.delta, ns[i], m, (int)D.variant);
         if (nst == 0) continue;
@@ -886,7 +910,9 @@ EPSM_API epsm_status epsm_create(epsm_ctx **out, int device, uint64_t flags) {
     if (!c) return EPSM_ERR_NOMEM;
     c->errbuf[0] = 0;
     c->device = device;
-    for (uint32_t m = 0; m <= EPSM_MAX_M; ++m) c->variant[m] = m ? default_variant(m) : 0;
+    for (int b = 0; b < EPSM_TEXT_BUCKETS; ++b)
+        for (uint32_t m = 0; m <= EPSM_MAX_M; ++m)
+            c->tune[b][m] = Tune{m ? default_variant(m) : 0, stream::kDefaultShape, (uint32_t)kHashBitsDefault};
     auto fail = [&](epsm_status st) {
         epsm_destroy(c);
         return st;
@@ -1104,13 +1130,39 @@ EPSM_API epsm_status epsm_search_host(epsm_ctx *c, const uint8_t *text_host, uin
 
 EPSM_API int epsm_variant_for(epsm_ctx *c, uint32_t m) {
     if (!c || m == 0 || m > EPSM_MAX_M) return 0;
-    return c->variant[m];
+    return c->tune[EPSM_TEXT_BUCKETS - 1][m].variant;
 }
 
 EPSM_API epsm_status epsm_set_variant(epsm_ctx *c, uint32_t m, int variant) {
     if (!c || m == 0 || m > EPSM_MAX_M) return EPSM_ERR_ARG;
     if (!variant_covers(variant, m)) return EPSM_ERR_ARG;
-    c->variant[m] = variant;
+    for (int b = 0; b < EPSM_TEXT_BUCKETS; ++b) c->tune[b][m].variant = variant;
+    return EPSM_OK;
+}
+
+EPSM_API epsm_status epsm_set_tuning(epsm_ctx *c, int bucket, uint32_t m, int variant, int shape,
+                                     uint32_t kbits) {
+    if (!c || m == 0 || m > EPSM_MAX_M || bucket < -1 || bucket >= EPSM_TEXT_BUCKETS) return EPSM_ERR_ARG;
+    if (variant != EPSM_VARIANT_AUTO && !variant_covers(variant, m)) return EPSM_ERR_ARG;
+    if (shape < -1 || shape >= stream::kShapes) return EPSM_ERR_ARG;
+    if (kbits != 0 && (kbits < EPSM_KBITS_MIN || kbits > EPSM_KBITS_MAX)) return EPSM_ERR_ARG;
+    for (int b = 0; b < EPSM_TEXT_BUCKETS; ++b) {
+        if (bucket >= 0 && b != bucket) continue;
+        Tune &T = c->tune[b][m];
+        if (variant != EPSM_VARIANT_AUTO) T.variant = variant;
+        if (shape >= 0) T.shape = shape;
+        if (kbits) T.kbits = kbits;
+    }
+    return EPSM_OK;
+}
+
+EPSM_API epsm_status epsm_get_tuning(epsm_ctx *c, int bucket, uint32_t m, int *variant, int *shape,
+                                     uint32_t *kbits) {
+    if (!c || m == 0 || m > EPSM_MAX_M || bucket < 0 || bucket >= EPSM_TEXT_BUCKETS) return EPSM_ERR_ARG;
+    const Tune &T = c->tune[bucket][m];
+    if (variant) *variant = T.variant;
+    if (shape) *shape = T.shape;
+    if (kbits) *kbits = T.kbits;
     return EPSM_OK;
 }
 
@@ -1212,7 +1264,7 @@ EPSM_API epsm_status epsm_search_static(const uint8_t *text, uint64_t n, const u
     p.err = reinterpret_cast<uint32_t *>(result_dev + 1);
     p.misc = D.misc;
     p.range_total = reinterpret_cast<unsigned long long *>(reinterpret_cast<uint8_t *>(D.misc) + 256);
-    if (launch_stream(D.sms, v, m, p, s) != cudaSuccess) return EPSM_ERR_CUDA;
+    if (launch_stream(D.sms, v, m, stream::kDefaultShape, p, s) != cudaSuccess) return EPSM_ERR_CUDA;
     return EPSM_OK;
 }
 

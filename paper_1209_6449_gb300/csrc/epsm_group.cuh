@@ -47,6 +47,7 @@ namespace group {
 using namespace stream;
 
 constexpr int kRing = 3;                 // stages in flight per block
+constexpr int kGroupBlocksPerSm = 2;     // resident blocks per SM the registers are set for
 constexpr int kSlotBits = 12;
 constexpr int kSlots = 1 << kSlotBits;   // head slots of the shared table
 constexpr int kMaxEnt = 1536;            // window entries per group
@@ -1054,7 +1055,7 @@ __device__ __forceinline__ void emit_range(const Params &P, const Header &H, Emi
 
 }  // namespace group
 
-__global__ void __launch_bounds__(stream::kThreadsStream, stream::kMaxBlocksPerSm)
+__global__ void __launch_bounds__(stream::kThreadsStream, group::kGroupBlocksPerSm)
     group_kernel(const __grid_constant__ group::Params P) {
     using namespace group;
     extern __shared__ __align__(128) uint8_t smem_raw[];

@@ -38,11 +38,17 @@ constexpr int kThreadsStream = (kConsumerWarps + 1) * 32;  // + producer warp
 constexpr int kStageChunks = kConsumerWarps * 128;          // 1024 chunks = 16 KiB
 constexpr uint64_t kStageBytes = (uint64_t)kStageChunks * 16u;
 constexpr int kStageBuf = (int)kStageBytes + 128;           // + halo chunk, 128-B aligned
-constexpr int kStages = 6;                                  // ring depth (96 KiB in flight per block)
+// Launch shapes of the filter kernel: ring depth (16 KiB stages in flight per
+// block) and resident blocks per SM, whose shared memory must fit an SM.  A
+// search's shape comes from the tuning table (shape 1 by default).
+template <int SH> struct Shape;
+template <> struct Shape<0> { static constexpr int stages = 6, blocks = 2; };  // 99 KiB x 2
+template <> struct Shape<1> { static constexpr int stages = 4, blocks = 3; };  // 66 KiB x 3
+constexpr int kShapes = 2;
+constexpr int kDefaultShape = 1;
 constexpr int kSegChunks = 128;                             // chunks per segment (2 KiB)
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int kConsumerBarrier = 1;                         // named barrier of consumer warps
-constexpr int kMaxBlocksPerSm = 2;
 constexpr uint64_t kMaxBlocks = 512;                        // grid bound (range totals, status words)
 
 constexpr uint32_t kClaim = 2;                              // stages per claim
@@ -62,7 +68,9 @@ __device__ __forceinline__ bool use_records(uint32_t hits, uint32_t nz) {
 constexpr int kAdaptDense = 2;   // probe: steps of 4 with a block match somewhere => dense text
 constexpr uint64_t kEndStage = ~0ull;
 
+template <int NS>
 struct alignas(128) StreamSmem {
+    static constexpr int kStages = NS;
     uint8_t buf[kStages][kStageBuf];
     uint64_t stage_id[kStages];  // global stage held by each ring slot (kEndStage: done)
     alignas(16) uint32_t wcnt[kStages][kConsumerWarps];  // per slot: the segments' hit counts
@@ -175,7 +183,8 @@ __device__ __forceinline__ uint4 staged_chunk(const SearchJob &J, uint64_t cf0, 
 // phase 1 roles
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void issue_stage(const StreamParams &P, StreamSmem &S, int s,
+template <typename SMEM>
+__device__ __forceinline__ void issue_stage(const StreamParams &P, SMEM &S, int s,
                                             uint64_t st) {
     const SearchJob &J = P.job;
     S.stage_id[s] = st;
@@ -199,7 +208,8 @@ __device__ __forceinline__ void issue_stage(const StreamParams &P, StreamSmem &S
 // Publishes the counts of the stage a ring slot held, once its consumers
 // released it: the eight segment counts as two 16-byte stores, and the stage
 // total added to its range total.
-__device__ __forceinline__ void flush_slot(const StreamParams &P, StreamSmem &S, int s) {
+template <typename SMEM>
+__device__ __forceinline__ void flush_slot(const StreamParams &P, SMEM &S, int s) {
     const uint64_t st = S.stage_id[s];
     const uint4 a = *reinterpret_cast<const uint4 *>(&S.wcnt[s][0]);
     const uint4 b = *reinterpret_cast<const uint4 *>(&S.wcnt[s][4]);
@@ -213,7 +223,9 @@ __device__ __forceinline__ void flush_slot(const StreamParams &P, StreamSmem &S,
     if (tot) atomicAdd(&P.range_total[st / P.range_stages], (unsigned long long)tot);
 }
 
-__device__ __forceinline__ void producer(const StreamParams &P, StreamSmem &S) {
+template <typename SMEM>
+__device__ __forceinline__ void producer(const StreamParams &P, SMEM &S) {
+    constexpr int kStages = SMEM::kStages;
     static_assert(kConsumerWarps == 8, "flush_slot publishes eight counts");
     uint32_t issued = 0;
     uint32_t pend = 0;  // bit s: slot s holds a stage whose counts are not yet published
@@ -468,8 +480,8 @@ __device__ __forceinline__ void store_segment(const StreamParams &P, uint32_t *w
 // One segment of the warp's ring: wait for the next stage, filter the warp's
 // segment of it, release the buffer and store the results.  Returns false at
 // the end of the stream (or when a wait gave up, with *ok cleared).
-template <int V, int MP, bool PROBE>
-__device__ __forceinline__ bool one_segment(const StreamParams &P, StreamSmem &S, const BcastWords &B,
+template <int V, int MP, bool PROBE, typename SMEM>
+__device__ __forceinline__ bool one_segment(const StreamParams &P, SMEM &S, const BcastWords &B,
                                             int &s, uint32_t &phase, int w, int lane, bool *ok,
                                             uint64_t &acc, bool *dense) {
     if (!warp_wait(&S.full[s], phase)) { *ok = false; return false; }
@@ -483,12 +495,12 @@ __device__ __forceinline__ bool one_segment(const StreamParams &P, StreamSmem &S
     // the stage buffer is no longer needed: release it to the producer
     __syncwarp();
     if (lane == 0) mbar_arrive(&S.empty[s]);
-    if (++s == kStages) { s = 0; phase ^= 1u; }
+    if (++s == SMEM::kStages) { s = 0; phase ^= 1u; }
     return true;
 }
 
-template <int V, int MP>
-__device__ __forceinline__ void filter_stages(const StreamParams &P, StreamSmem &S, int w, int lane,
+template <int V, int MP, typename SMEM>
+__device__ __forceinline__ void filter_stages(const StreamParams &P, SMEM &S, int w, int lane,
                                               bool *ok) {
     const BcastWords B(P.job.pat);
     int s = 0;
@@ -614,7 +626,10 @@ __device__ __forceinline__ uint2 load_masks(const uint16_t *seg_mask, uint64_t s
 // first + j has hits; lane j holds its exclusive output offset in `excl`).  The
 // masks of up to kEmitAhead segments are loaded together before they are
 // emitted, so the L2 latency of the mask loads is paid once per group.
-constexpr int kEmitAhead = 4;
+#ifndef EPSM_EMIT_AHEAD
+#define EPSM_EMIT_AHEAD 4
+#endif
+constexpr int kEmitAhead = EPSM_EMIT_AHEAD;
 
 template <typename EmitFn>
 __device__ __forceinline__ void emit_list(uint32_t todo, uint64_t first, uint64_t excl,
@@ -799,12 +814,14 @@ __device__ __forceinline__ void finish_stream(const StreamParams &P) {
 
 }  // namespace stream
 
-template <int V, int MP>
-__global__ void __launch_bounds__(stream::kThreadsStream, stream::kMaxBlocksPerSm)
+template <int V, int MP, int SH>
+__global__ void __launch_bounds__(stream::kThreadsStream, stream::Shape<SH>::blocks)
     stream_kernel(const __grid_constant__ stream::StreamParams P) {
     using namespace stream;
+    using SMEM = StreamSmem<Shape<SH>::stages>;
+    constexpr int kStages = SMEM::kStages;
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    StreamSmem &S = *reinterpret_cast<StreamSmem *>(smem_raw);
+    SMEM &S = *reinterpret_cast<SMEM *>(smem_raw);
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -841,7 +858,12 @@ __global__ void __launch_bounds__(stream::kThreadsStream, stream::kMaxBlocksPerS
 // slices, then claims ranges dynamically and emits them in order; block 0
 // writes the total, and the last block clears the range totals and the claim
 // counters for the next search.
-__global__ void __launch_bounds__(stream::kEmitThreads, 4)
+// Emission blocks resident per SM that the register budget is set for (a
+// build-time tuning knob).
+#ifndef EPSM_EMIT_MIN_BLOCKS
+#define EPSM_EMIT_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(stream::kEmitThreads, EPSM_EMIT_MIN_BLOCKS)
     stream_emit_kernel(const __grid_constant__ stream::StreamParams P) {
     using namespace stream;
     __shared__ StreamEmitSmem S;

@@ -15,7 +15,7 @@ _lib = _native.load()
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_uint32), ("inflight", ctypes.c_uint32),
-                ("per_query", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("per_query", ctypes.c_uint32), ("small_batch", ctypes.c_uint32),
                 ("upload_budget", ctypes.c_uint64), ("reserve", ctypes.c_uint64),
                 ("out_capacity", ctypes.c_uint64)]
 
@@ -54,9 +54,9 @@ class Server:
 
     def __init__(self, device: int = 0, max_batch: int = 1024, inflight: int = 2,
                  per_query: bool = False, upload_budget: int = 0, reserve: int = 0,
-                 out_capacity: int = 0):
-        cfg = ServerConfig(max_batch, inflight, 1 if per_query else 0, 0, upload_budget, reserve,
-                           out_capacity)
+                 out_capacity: int = 0, small_batch: int = 0):
+        cfg = ServerConfig(max_batch, inflight, 1 if per_query else 0, small_batch, upload_budget,
+                           reserve, out_capacity)
         h = ctypes.c_void_p()
         _check(_lib.epsm_server_create(ctypes.byref(h), device, ctypes.byref(cfg)), "epsm_server_create")
         self.handle = h
@@ -121,6 +121,12 @@ class Server:
 
     def release(self, request: int):
         _check(_lib.epsm_server_release(self.handle, request), "epsm_server_release")
+
+    FAULT_ALLOC, FAULT_ADMIT, FAULT_UPLOAD = 0, 1, 2
+
+    def inject_fault(self, kind: int, count: int = 1):
+        """Arms `count` host-side failures of one kind (see epsm_server_inject_fault)."""
+        _check(_lib.epsm_server_inject_fault(self.handle, kind, count), "epsm_server_inject_fault")
 
     def stats(self) -> dict:
         s = Stats()

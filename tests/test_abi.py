@@ -75,6 +75,7 @@ def test_server_arguments_checked_on_the_host():
     assert lib.epsm_server_poll(None, None, 4, 0) == 0
     assert lib.epsm_server_release(None, 1) == 1
     assert lib.epsm_server_read(None, 1, None, 0) == 1
+    assert lib.epsm_server_inject_fault(None, 0, 1) == 1
 
 
 def test_missing_library_fails_loudly(tmp_path):
@@ -99,19 +100,36 @@ def test_package_does_not_reach_the_oracle():
 
 
 def test_shipped_tuning_table_is_consistent():
-    """tuning.json (written by the autotuner on a GPU) names, for every m in
-    1..32, a variant that covers m; the names match the variant numbers."""
+    """tuning.json (written by the autotuner on a GPU) names, for every
+    alphabet class, text-length bucket and m in 1..32, a variant that covers
+    m, a launch shape and a fingerprint width in range."""
     import json
     path = os.path.join(ROOT, "paper_1209_6449_gb300", "tuning.json")
     if not os.path.exists(path):
         pytest.skip("no tuning table shipped")
     with open(path) as f:
         tab = json.load(f)
+    assert tab["version"] == 2
     cover = {1: range(1, 5), 2: range(4, 16), 3: range(8, 16), 4: range(15, 33), 5: range(7, 17),
              6: range(2, 17), 7: range(5, 17), 8: range(23, 33)}
     names = {1: "direct", 2: "prefix4", 3: "prefix8", 4: "block8", 5: "block4", 6: "code2",
              7: "adapt", 8: "block8s"}
-    assert sorted(int(m) for m in tab["variant"]) == list(range(1, 33))
-    for m, v in tab["variant"].items():
-        assert int(m) in cover[v], (m, v)
-        assert tab["names"][m] == names[v]
+    assert {"dna", "protein", "text", "mixed"} <= set(tab["classes"])
+    for cls, rows in tab["classes"].items():
+        assert sorted(int(b) for b in rows) == [0, 1, 2], cls
+        for b, by_m in rows.items():
+            assert sorted(int(m) for m in by_m) == list(range(1, 33)), (cls, b)
+            for m, r in by_m.items():
+                assert int(m) in cover[r["variant"]], (cls, b, m, r)
+                assert r["name"] == names[r["variant"]]
+                assert r["shape"] in (0, 1) and 8 <= r["kbits"] <= 14
+
+
+def test_tuning_bucket_bounds_match_header():
+    import re as _re
+    from paper_1209_6449_gb300 import _native
+    src = open(os.path.join(ROOT, "include", "epsm.h")).read()
+    b1 = int(_re.search(r"EPSM_BUCKET1_MIN \((\d+)ull << (\d+)\)", src).group(1)) << 20
+    b2 = int(_re.search(r"EPSM_BUCKET2_MIN \((\d+)ull << (\d+)\)", src).group(1)) << 20
+    assert _native.BUCKET_MIN == (0, b1, b2)
+    assert [_native.text_bucket(n) for n in (0, b1 - 1, b1, b2 - 1, b2)] == [0, 0, 1, 1, 2]

@@ -122,17 +122,48 @@ def test_batch_graph_replay_and_reuse(ctx, torch):
 
 @pytest.mark.gpu
 def test_autotuner_small_run():
-    """The autotuner measures every variant that covers each m and returns a
-    table of variants that cover their m; the context accepts it."""
+    """The autotuner measures every candidate (variant, launch shape,
+    fingerprint width) for each m and returns rows that cover their m; the
+    context accepts them, and searches stay exact under every configuration
+    it tried."""
     import paper_1209_6449_gb300 as epsm
     from paper_1209_6449_gb300 import autotune
     ctx = epsm.Context(0, tuning=None)
     try:
-        res = autotune.autotune(ctx, n=1 << 20, ms=(2, 6, 9, 20), reps=1, patterns=1)
-        for m, v in res["variant"].items():
-            assert int(m) in autotune.COVER[v], (m, v)
-            assert set(res["ms_per_search"][m]) == {epsm.VARIANT_NAMES[x] for x in autotune.variants_for(int(m))}
-        autotune.apply(ctx, res)
-        assert all(ctx.variant_for(int(m)) == v for m, v in res["variant"].items())
+        res = autotune.autotune(ctx, ms=(2, 6, 9, 20, 27), buckets=(0,), classes=("dna", "text"),
+                                bucket_n=(1 << 20,), reps=1, patterns=1)
+        for cls in ("dna", "text", "mixed"):
+            for m, r in res["classes"][cls]["0"].items():
+                assert int(m) in autotune.COVER[r["variant"]], (cls, m, r)
+                assert (r["variant"], r["shape"], r["kbits"]) in autotune.candidates(int(m))
+        for m in (2, 6, 9, 20, 27):
+            assert len(res["ms"]["dna"]["0"][str(m)]) == len(autotune.candidates(m))
+        autotune.apply(ctx, res, "dna")
+        for m, r in res["classes"]["dna"]["0"].items():
+            assert ctx.get_tuning(0, int(m)) == (r["variant"], r["shape"], r["kbits"])
+        # every configuration the tuner can pick gives the oracle's result
+        host = gen.TextSpec("dna", 5).host((1 << 20) + 9)
+        dev = __import__("torch").from_numpy(host).cuda()
+        for m in (6, 27):
+            p = gen.planted_patterns(gen.TextSpec("dna", 5), host.size, m, 1)[0]
+            want = oracle.search(host, p)
+            for v, sh, kb in autotune.candidates(m):
+                ctx.set_tuning(-1, m, v, sh, kb)
+                cnt, pos = ctx.search(dev, p, capacity=want.size + 8)
+                assert cnt == want.size and (pos.cpu().numpy().astype("uint64") == want).all(), (v, sh, kb)
     finally:
         ctx.close()
+
+
+@pytest.mark.gpu
+def test_tuning_entry_points(ctx):
+    import paper_1209_6449_gb300 as epsm
+    h = ctx.handle
+    assert epsm.epsm_set_tuning(h, 3, 5) == 1          # no such bucket
+    assert epsm.epsm_set_tuning(h, 0, 3, epsm.VARIANT_BLOCK8) == 1  # does not cover m
+    assert epsm.epsm_set_tuning(h, 0, 20, 0, 2) == 1   # no such shape
+    assert epsm.epsm_set_tuning(h, 0, 20, 0, -1, 15) == 1  # width out of range
+    assert epsm.epsm_set_tuning(h, 1, 20, epsm.VARIANT_BLOCK8, 0, 11) == 0
+    assert epsm.epsm_get_tuning(h, 1, 20) == (0, epsm.VARIANT_BLOCK8, 0, 11)
+    assert epsm.epsm_set_tuning(h, -1, 20, 0, -1, 12) == 0   # keep variant and shape
+    assert epsm.epsm_get_tuning(h, 1, 20) == (0, epsm.VARIANT_BLOCK8, 0, 12)

@@ -177,3 +177,84 @@ def test_replay_counts_and_latencies(corpora, torch):
         assert srv.stats()["uploads"] == 1
     finally:
         srv.close()
+
+
+def _one(srv, timeout=30.0):
+    r = srv.poll(1, timeout_s=timeout)
+    assert len(r) == 1
+    return r[0]
+
+
+def test_injected_buffer_failure_fails_the_batch_and_serving_continues(corpora, torch):
+    """A failure to obtain an output buffer (injected on the host) fails the
+    queries of that batch with EPSM_ERR_NOMEM; the next queries are served
+    exactly."""
+    import paper_1209_6449_gb300 as epsm
+    srv = epsm.Server(0, max_batch=16, inflight=1)
+    try:
+        for _, _, t in corpora:
+            srv.add_corpus(t)
+        srv.inject_fault(srv.FAULT_ALLOC, 1)
+        p = bytes(corpora[1][1][5000:5009])
+        rid = srv.submit(1, p)
+        r = _one(srv)
+        assert r["request"] == rid and r["status"] == 4 and r["count"] == 0  # EPSM_ERR_NOMEM
+        for c in range(len(corpora)):
+            q = bytes(corpora[c][1][777:777 + 6 + c])
+            rid = srv.submit(c, q)
+            r = _one(srv)
+            assert r["request"] == rid and r["status"] == 0
+            assert np.array_equal(srv.read(rid, r["count"]), oracle.search(corpora[c][1], q))
+            srv.release(rid)
+    finally:
+        srv.close()
+
+
+def test_injected_admission_and_upload_failures(corpora, torch):
+    """Admission refused, then an upload copy failed (both injected on the
+    host): those uploads complete with EPSM_ERR_NOMEM and EPSM_ERR_CUDA, hold no
+    memory, and the next upload is admitted and searchable."""
+    import paper_1209_6449_gb300 as epsm
+    n = 1 << 20
+    srv = epsm.Server(0, max_batch=16, upload_budget=2 * (n + 16))
+    try:
+        host = gen.TextSpec("protein", 301).host(n)
+        srv.inject_fault(srv.FAULT_ADMIT, 1)
+        srv.upload(host)
+        assert _one(srv)["status"] == 4      # EPSM_ERR_NOMEM
+        srv.inject_fault(srv.FAULT_UPLOAD, 1)
+        srv.upload(host)
+        assert _one(srv)["status"] == 3      # EPSM_ERR_CUDA
+        assert srv.stats()["uploads"] == 0
+        srv.upload(host)
+        r = _one(srv)
+        assert r["status"] == 0 and r["count"] == n
+        cid = r["corpus"]
+        p = bytes(host[4242:4254])
+        rid = srv.submit(cid, p)
+        q = _one(srv)
+        assert q["request"] == rid and q["status"] == 0
+        assert np.array_equal(srv.read(rid, q["count"]), oracle.search(host, p))
+        srv.release(rid)
+        # the two failed uploads left the budget free: a second text fits
+        srv.upload(host)
+        assert _one(srv)["status"] == 0
+        assert srv.stats()["evictions"] == 0
+    finally:
+        srv.close()
+
+
+def test_faults_armed_from_the_environment(corpora, torch, monkeypatch):
+    import paper_1209_6449_gb300 as epsm
+    monkeypatch.setenv("EPSM_FAULT", "alloc:2,bogus:3")
+    srv = epsm.Server(0, max_batch=1, inflight=1)
+    monkeypatch.delenv("EPSM_FAULT")
+    try:
+        srv.add_corpus(corpora[0][2])
+        st = []
+        for k in range(3):
+            srv.submit(0, b"ACGTA"[:2 + k])
+            st.append(_one(srv)["status"])
+        assert st == [4, 4, 0]
+    finally:
+        srv.close()
