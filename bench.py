@@ -106,7 +106,7 @@ def run_case(args):
     variant = int(parts[2]) if len(parts) > 2 and parts[2] else 0
     n = int(parts[3]) if len(parts) > 3 and parts[3] else TEXT_N
     mode = parts[4] if len(parts) > 4 else ""
-    ctx = epsm.Context(0)
+    ctx = epsm.Context(0, text_class=KIND_CLASS.get(kind, "mixed"))
     spec = gen.TextSpec(kind, 0)
     t = torch.empty(n, dtype=torch.uint8, device="cuda")
     spec.device(n, t.data_ptr(), torch.cuda.current_stream().cuda_stream)
@@ -562,13 +562,13 @@ def run_e2e(ctx, torch, texts, pats, steps, warmup, occ, dist=None):
     """The same workload through epsm_search_host (host text in, host positions
     out): every step copies each text from pinned host memory to the device,
     runs its single searches and copies all positions back.  One call per text
-    with all its patterns when the pinned buffers fit in a third of the host's
+    with all its patterns when the pinned buffers fit in 55% of the host's
     available memory; otherwise a text's patterns are split over several calls
     (each uploads the text again, counted in h2d_bytes_per_step)."""
     from paper_1209_6449_gb300 import epsm_search_host
     kinds = list(dict.fromkeys(k for (k, _, _, _) in pats))
     text_bytes = sum(texts[k].numel() for k in kinds)
-    budget = max(_mem_available() // 3 - text_bytes, 1 << 30)
+    budget = max(_mem_available() * 11 // 20 - text_bytes, 1 << 30)
     cap = max(int(occ.max()) + 1024, min(budget // 8, int(occ.sum()) + 1024))
     calls = []  # (text kind, patterns)
     for k in kinds:

@@ -226,6 +226,10 @@ struct epsm_ctx {
     // pattern bytes past the first 32 of a long pattern (m > EPSM_MAX_M)
     uint8_t *tail = nullptr;
     uint32_t tail_cap = 0;
+    // host end-to-end: copies of finished patterns' positions overlap the
+    // next pattern's search
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_ev = nullptr;
 };
 
 namespace {
@@ -948,6 +952,8 @@ EPSM_API epsm_status epsm_destroy(epsm_ctx *c) {
     if (c->dtext) cudaFree(c->dtext);
     if (c->dpos) cudaFree(c->dpos);
     if (c->tail) cudaFree(c->tail);
+    if (c->copy_ev) cudaEventDestroy(c->copy_ev);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->ev) cudaEventDestroy(c->ev);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -1102,9 +1108,14 @@ EPSM_API epsm_status epsm_search_host(epsm_ctx *c, const uint8_t *text_host, uin
     epsm_status st = order_after_previous(c, s);
     if (st != EPSM_OK) return st;
     if (n) CK(cudaMemcpyAsync(c->dtext, text_host, n, cudaMemcpyHostToDevice, s));
+    if (!c->copy_stream) {
+        CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->copy_ev, cudaEventDisableTiming));
+    }
     // one single search per pattern (the kernels of epsm_search), each writing
     // its positions right after the previous pattern's; the count comes back
-    // after each search, and the positions are copied back once at the end
+    // after each search, and that pattern's positions are copied back on a
+    // second stream while the next pattern is searched
     uint64_t off = 0;
     uint64_t p0 = 0;
     for (uint32_t k = 0; k < npat; ++k) {
@@ -1116,15 +1127,19 @@ EPSM_API epsm_status epsm_search_host(epsm_ctx *c, const uint8_t *text_host, uin
         uint32_t err = 0;
         if ((st = read_misc(c, s, &err)) != EPSM_OK) return st;
         if (err & kErrTimeout) return EPSM_ERR_TIMEOUT;
-        off += c->hmisc->count;
+        const uint64_t cnt = c->hmisc->count;
+        const uint64_t got = std::min<uint64_t>(cnt, room);
+        if (got) {
+            CK(cudaEventRecord(c->copy_ev, s));
+            CK(cudaStreamWaitEvent(c->copy_stream, c->copy_ev, 0));
+            CK(cudaMemcpyAsync(positions_host + off, c->dpos + off, got * sizeof(uint64_t),
+                               cudaMemcpyDeviceToHost, c->copy_stream));
+        }
+        off += cnt;
         p0 += ms[k];
     }
     offsets_host[npat] = off;
-    const uint64_t got = std::min<uint64_t>(off, capacity);
-    if (got) {
-        CK(cudaMemcpyAsync(positions_host, c->dpos, got * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-    }
+    CK(cudaStreamSynchronize(c->copy_stream));
     return off > capacity ? EPSM_ERR_CAPACITY : EPSM_OK;
 }
 

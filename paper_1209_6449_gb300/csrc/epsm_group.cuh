@@ -1151,7 +1151,13 @@ __global__ void __launch_bounds__(stream::kEmitThreads, 4)
         __syncthreads();
         const uint64_t st0 = (uint64_t)r * H.range_stages;
         const uint64_t st1 = st0 + H.range_stages < H.jstages ? st0 + H.range_stages : H.jstages;
-        if (st0 < st1) emit_range(P, H, S, st0, st1, S.range_base, warp, lane);
+        if (st0 < st1 && rt[r] != 0ull) {
+            emit_range(P, H, S, st0, st1, S.range_base, warp, lane);
+        } else if (st0 < st1 && t == 0) {
+            // no hits in the range: the jobs starting in it begin at its base
+            for (uint32_t j = first_job_from(P.jobs, H.njobs, st0); j < H.njobs && P.jobs[j].stage0 < st1; ++j)
+                P.offsets[j] = S.range_base;
+        }
         __syncthreads();
     }
     if (t == 0) {

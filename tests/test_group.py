@@ -141,3 +141,19 @@ def test_group_edges(ctx, torch):
             views.append(v)
             hosts.append(h)
     _check(ctx, torch, views, hosts, pats * 9)
+
+
+def test_short_patterns_share_two_byte_windows(ctx, torch):
+    """Short patterns (m 2..4) of a group over a large alphabet share the
+    2-byte window table; where their hits are dense the per-warp list
+    overflows and each is redone alone with the masked direct compare."""
+    rng = np.random.default_rng(12)
+    host = gen.TextSpec("protein", 31).host(400_000).copy()
+    host[50_000:90_000] = np.frombuffer(b"ab" * 20_000, dtype=np.uint8)      # dense "ab" stretch
+    host[200_000:200_300] = ord("Q")
+    buf, view = _dev(torch, host, off=6)
+    pats = [b"ab", b"ba", b"aba", b"abab", b"QQ", b"QQQ", b"QQQQ", b"AC", b"DEF", b"KLMN"]
+    for m in (2, 3, 4, 5, 9, 13, 20):
+        pats += gen.mixed_patterns(gen.TextSpec("protein", 31), host.size, m, 2, stream_seed=m)
+    pats += [bytes(host[o:o + int(rng.integers(2, 5))]) for o in rng.integers(0, host.size - 5, 20)]
+    _check(ctx, torch, [view] * len(pats), [host] * len(pats), pats)
