@@ -681,9 +681,10 @@ uint32_t shared_stride(uint32_t m) {
 }
 
 // Pairs on the same text (same pointer and length) are searched in shared
-// passes: one group per text (more if its patterns exceed the per-group
-// limits), with a shared filter over its patterns of stride K > 0 and the
-// others run one by one on the staged bytes.
+// passes: per text one group of the short patterns, run one by one on the
+// staged bytes, and one group per window width of the patterns of stride
+// K > 0, searched through a shared filter (more groups where a kind exceeds
+// the per-group limits).
 epsm_status batch_submit(epsm_ctx *c, uint32_t npairs, const uint8_t *const *texts,
                          const uint64_t *ns, const uint8_t *const *patterns, const uint32_t *ms,
                          uint64_t *positions, uint64_t capacity, cudaStream_t s) {
@@ -754,56 +755,65 @@ epsm_status batch_submit(epsm_ctx *c, uint32_t npairs, const uint8_t *const *tex
     RB.pend_nj = nj;
     RB.pend_capacity = capacity;
     if (nj == 0) return mark_done(c, s);
-    // groups: per text, shared patterns up to kMaxShared / kMaxEnt entries and
-    // individual ones up to kIndivMax per group
+    // groups: per text and kind, shared patterns up to kMaxShared / kMaxEnt
+    // entries or individual ones up to kIndivMax per group
     std::vector<GroupDesc> groups;
     std::vector<uint32_t> gjobs;
     gjobs.reserve(nj);
     uint32_t ncomb = 0;
     uint64_t gst = 0;
-    std::vector<uint32_t> sh, ind;
+    // Each text's patterns form up to three kinds of group, searched as
+    // separate passes over the text: the short ones (direct compare), the
+    // shared filter with 4-byte windows and the one with 8-byte windows.  Kept
+    // apart, each pass runs at the pace of its own kind instead of the slowest
+    // kind's (the short patterns' many hits hold up a combined pass).
+    std::vector<uint32_t> cls[3];
     for (size_t r = 0; r + 1 < runs.size(); ++r) {
-        sh.clear();
-        ind.clear();
+        for (auto &v : cls) v.clear();
         for (uint32_t k = runs[r]; k < runs[r + 1]; ++k) {
             const uint32_t pi = order[k];
             if (jidx[pi] < 0) continue;
-            (kstr[pi] ? sh : ind).push_back((uint32_t)jidx[pi]);
+            cls[!kstr[pi] ? 0 : ms[pi] < kW8Min ? 1 : 2].push_back((uint32_t)jidx[pi]);
         }
-        size_t ps = 0, pi = 0;
-        while (ps < sh.size() || pi < ind.size()) {
-            GroupDesc G;
-            memset(&G, 0, sizeof(G));
-            G.job0 = (uint32_t)gjobs.size();
-            uint64_t nst = 0;
-            uint32_t k8 = 0, k4 = 0;
-            while (ps < sh.size() && G.nshared < (uint32_t)kMaxShared &&
-                   G.nent + kept[sh[ps]].kstride <= (uint32_t)kMaxEnt) {
-                JobDesc &D = kept[sh[ps++]];
-                D.ent0 = G.nent;
-                G.nent += D.kstride;
-                ++G.nshared;
-                gjobs.push_back((uint32_t)(&D - kept.data()));
-                nst = std::max(nst, D.nstages);
-                uint32_t &k = D.job.pat.m >= kW8Min ? k8 : k4;
-                k = k ? std::min(k, D.kstride) : D.kstride;
+        for (int kc = 0; kc < 3; ++kc) {
+            const std::vector<uint32_t> &L = cls[kc];
+            size_t pos = 0;
+            while (pos < L.size()) {
+                GroupDesc G;
+                memset(&G, 0, sizeof(G));
+                G.job0 = (uint32_t)gjobs.size();
+                uint64_t nst = 0;
+                uint32_t kmin = 0;
+                if (kc == 0) {
+                    while (pos < L.size() && G.nindiv < (uint32_t)kIndivMax) {
+                        const uint32_t jj = L[pos++];
+                        ++G.nindiv;
+                        gjobs.push_back(jj);
+                        nst = std::max(nst, kept[jj].nstages);
+                    }
+                } else {
+                    while (pos < L.size() && G.nshared < (uint32_t)kMaxShared &&
+                           G.nent + kept[L[pos]].kstride <= (uint32_t)kMaxEnt) {
+                        JobDesc &D = kept[L[pos++]];
+                        D.ent0 = G.nent;
+                        G.nent += D.kstride;
+                        ++G.nshared;
+                        gjobs.push_back((uint32_t)(&D - kept.data()));
+                        nst = std::max(nst, D.nstages);
+                        kmin = kmin ? std::min(kmin, D.kstride) : D.kstride;
+                    }
+                }
+                const JobDesc &D0 = kept[gjobs[G.job0]];
+                G.text = D0.job;
+                G.chunk_full0 = (D0.job.delta + 15u) / 16u;
+                G.chunk_full1 = D0.job.lim / 16u;
+                G.gstage0 = gst;
+                G.nstages = nst;
+                G.cfg = kc == 2 ? kmin : (kmin << 8);
+                G.comb = (G.nshared || G.nindiv > 1u) ? ncomb++ : kNone;
+                gst += nst;
+                groups.push_back(G);
             }
-            while (pi < ind.size() && G.nindiv < (uint32_t)kIndivMax) {
-                const uint32_t jj = ind[pi++];
-                ++G.nindiv;
-                gjobs.push_back(jj);
-                nst = std::max(nst, kept[jj].nstages);
-            }
-            const JobDesc &D0 = kept[gjobs[G.job0]];
-            G.text = D0.job;
-            G.chunk_full0 = (D0.job.delta + 15u) / 16u;
-            G.chunk_full1 = D0.job.lim / 16u;
-            G.gstage0 = gst;
-            G.nstages = nst;
-            G.cfg = k8 | (k4 << 8);
-            G.comb = (G.nshared || G.nindiv > 1u) ? ncomb++ : kNone;
-            gst += nst;
-            groups.push_back(G);
         }
     }
     const uint32_t ng = (uint32_t)groups.size();
