@@ -357,11 +357,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+# the files the single search's kernels and their launch choices come from
+# (the batched and served forms, and the host runtime, do not change them)
+SINGLE_SEARCH_SOURCES = ("csrc/epsm_kernels.cuh", "csrc/epsm_scan.cuh", "csrc/epsm_stream.cuh",
+                         "csrc/epsm_tile.cuh", "tuning.json")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1209_6449_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
+    pkg = os.path.join(ROOT, "paper_1209_6449_gb300")
+    for f in SINGLE_SEARCH_SOURCES:
+        with open(os.path.join(pkg, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
