@@ -357,7 +357,10 @@ __device__ __forceinline__ uint32_t segment_hits(const SearchJob &J, const uint4
                 const uint32_t n2 = __shfl_sync(kFull, nsrc.z, src);
                 const uint32_t n3 = __shfl_sync(kFull, nsrc.w, src);
                 const uint32_t cand = z ? even_bits(z) : 0u;
-                if (__any_sync(kFull, __popc(cand) > 3)) {
+                if (pat.q == 1u) {
+                    // one byte repeated: the chunk's starts decided at once
+                    hh = cand ? run_chunk_regs(pat, ch[u], n0, n1, n2, n3) & cand : 0u;
+                } else if (__any_sync(kFull, __popc(cand) > 3)) {
                     // many candidates somewhere in the warp (a run of one
                     // byte): all 16 starts checked at once on the bytes
                     hh = cand ? exact_chunk_regs(pat, ch[u], n0, n1, n2, n3) & cand : 0u;

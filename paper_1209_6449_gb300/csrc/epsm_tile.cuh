@@ -136,6 +136,62 @@ __device__ __noinline__ uint32_t exact_chunk_regs(const Pattern &pat, const uint
     return exact_starts16<8>(R, pat);
 }
 
+// Exact hits of the 16 starts p0 .. p0+15 for a pattern that is one byte
+// repeated m times (period 1), from text words R[] aligned at p0 that hold at
+// least 15 + m bytes.  With E the mask of the text bytes equal to that byte
+// (Section 3.2's packed compare against the broadcast byte: one compare per
+// text word whatever m is), start i is an occurrence iff bits i .. i+m-1 of E
+// are all set; doubling shift-ANDs find those runs of m ones in log2 m steps.
+// A run of that byte in the text makes every start a candidate of the
+// fingerprint and code filters; this decides a chunk's 16 starts at once.
+template <int NW>
+__device__ __forceinline__ uint32_t run_starts16(const uint32_t (&R)[NW], uint32_t bb, uint32_t m) {
+    static_assert(NW <= 16, "a 64-bit byte mask");
+    uint64_t E = 0ull;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) E |= (uint64_t)nibble_of(zero_bytes(R[k] ^ bb)) << (4 * k);
+    uint32_t L = 1u;  // bit i of E: bytes i .. i+L-1 all equal bb
+    while (2u * L <= m) {
+        E &= E >> L;
+        L *= 2u;
+    }
+    E &= E >> (m - L);
+    return (uint32_t)E & 0xFFFFu;
+}
+
+// run_starts16 on the bytes of a chunk and the next chunk (m <= 17); out of
+// line, so the filter loop keeps its registers.
+__device__ __noinline__ uint32_t run_chunk_regs(const Pattern &pat, const uint4 cur, uint32_t n0,
+                                                uint32_t n1, uint32_t n2, uint32_t n3) {
+    const uint32_t R[8] = {cur.x, cur.y, cur.z, cur.w, n0, n1, n2, n3};
+    return run_starts16<8>(R, bcast_byte(pat.w[0], 0), pat.m);
+}
+
+// run_starts16 on the text from p0 (any alignment; m <= 32): 12 words from
+// the staged bytes when they cover them, else from global memory (bytes
+// outside the text read as 0; the starts they reach are masked by the caller).
+__device__ __noinline__ uint32_t run_starts_staged(const SearchJob &J, int64_t p0, const StagedText &T) {
+    const int64_t wa = p0 >> 2;  // (floor: p0 may be negative at the text's start)
+    const uint32_t sh = (uint32_t)(p0 & 3) * 8u;
+    uint32_t W[13];
+    const int64_t o = wa * 4 - T.sbase;
+    if (T.inside && o >= 0 && o + 52 <= (int64_t)T.span) {
+        const uint32_t *S = reinterpret_cast<const uint32_t *>(T.buf) + (o >> 2);
+#pragma unroll
+        for (int k = 0; k < 13; ++k) W[k] = S[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 13; ++k) {
+            const int64_t wk = wa + k;
+            W[k] = wk < 0 ? 0u : load_word(J, (uint64_t)wk);
+        }
+    }
+    uint32_t R[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) R[k] = __funnelshift_r(W[k], W[k + 1], sh);
+    return run_starts16<12>(R, bcast_byte(J.pat.w[0], 0), J.pat.m);
+}
+
 // Candidates of the block variant: the chunk's two blocks (those whose
 // fingerprint slot is marked: t0, t1) compared with the pattern blocks
 // p[j..j+7]; a block match at j gives the candidate 8b - j (Section 3.4).
@@ -270,6 +326,18 @@ __device__ __noinline__ uint32_t block_slow(const SearchJob &J, const uint4 cur,
                                             const uint8_t *tail, uint32_t mtail) {
     const uint32_t cand = V == V_BLOCK8S ? (t0 ? block_cands16(cur, pblk) : 0u)
                                          : ((t0 | t1) ? block_cands8(cur, pblk, t0, t1) : 0u);
+    if (J.pat.q == 1u && J.pat.m <= 32u) {
+        // one byte repeated: the chunk's starts decided at once from the text
+        if (!cand) return 0u;
+        StagedText T;
+        T.buf = buf;
+        T.sbase = sbase;
+        T.span = (uint32_t)((1024 + 1) * 16);
+        T.inside = inside;
+        T.tail = tail;
+        T.mtail = mtail;
+        return run_starts_staged(J, p0, T) & cand;
+    }
     if (__any_sync(kFull, __popc(cand) > kCoopMin))
         return coop_verify(J, p0, cand, buf, sbase, inside, tail, mtail);
     if (!cand) return 0u;
