@@ -351,9 +351,13 @@ cudaError_t launch_stream_shape(int sms, int v, uint32_t m, stream::StreamParams
         case V_PREFIX4: return launch_stream_t<V_PREFIX4, 4, SH>(sms, p, s);
         case V_PREFIX8: return launch_stream_t<V_PREFIX8, 8, SH>(sms, p, s);
         case V_BLOCK4: return launch_stream_t<V_BLOCK4, 4, SH>(sms, p, s);
-        case V_CODE2: return launch_stream_t<V_CODE2, 4, SH>(sms, p, s);
+        case V_CODE2:  // (a pattern of period 1 has a kernel of its own)
+            return p.job.pat.q == 1u ? launch_stream_t<V_CODE2, kMpRun, SH>(sms, p, s)
+                                     : launch_stream_t<V_CODE2, 4, SH>(sms, p, s);
         case V_ADAPT: return launch_stream_t<V_ADAPT, 4, SH>(sms, p, s);
-        case V_BLOCK8S: return launch_stream_t<V_BLOCK8S, 8, SH>(sms, p, s);
+        case V_BLOCK8S:  // (a pattern of period 1 has a kernel of its own)
+            return p.job.pat.q == 1u && p.job.pat.m <= 32u ? launch_stream_t<V_BLOCK8S, kMpRun, SH>(sms, p, s)
+                                                           : launch_stream_t<V_BLOCK8S, 8, SH>(sms, p, s);
         default: return launch_stream_t<V_BLOCK8, 8, SH>(sms, p, s);
     }
 }

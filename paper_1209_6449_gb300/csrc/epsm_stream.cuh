@@ -357,9 +357,14 @@ __device__ __forceinline__ uint32_t segment_hits(const SearchJob &J, const uint4
                 const uint32_t n2 = __shfl_sync(kFull, nsrc.z, src);
                 const uint32_t n3 = __shfl_sync(kFull, nsrc.w, src);
                 const uint32_t cand = z ? even_bits(z) : 0u;
-                if (pat.q == 1u) {
-                    // one byte repeated: the chunk's starts decided at once
-                    hh = cand ? run_chunk_regs(pat, ch[u], n0, n1, n2, n3) & cand : 0u;
+                if constexpr (MP == kMpRun) {
+                    // one byte repeated (a kernel of its own): the chunk's
+                    // starts decided at once from the byte-equality masks of
+                    // the chunk and the next (that one from the next lane)
+                    const uint32_t bb = bcast_byte(pat.w[0], 0);
+                    const uint32_t e_own = eq_mask16(ch[u], bb);
+                    const uint32_t e_next = __shfl_sync(kFull, lane == 0 ? eq_mask16(nsrc, bb) : e_own, src);
+                    hh = cand ? runs_of(((uint64_t)e_next << 16) | e_own, pat.m) & cand : 0u;
                 } else if (__any_sync(kFull, __popc(cand) > 3)) {
                     // many candidates somewhere in the warp (a run of one
                     // byte): all 16 starts checked at once on the bytes
@@ -672,7 +677,7 @@ constexpr int kEmitWarps = 8;
 constexpr int kEmitThreads = kEmitWarps * 32;
 struct alignas(16) StreamEmitSmem {
     uint16_t emit_stage[kEmitWarps][32 * 16];  // per-warp staging of hit offsets
-    uint32_t scan_tmp[kEmitWarps];
+    uint32_t scan_tmp[2][kEmitWarps];            // per batch, alternating (one barrier a batch)
     uint64_t scan64[kEmitWarps];
     uint64_t slice_pre[kEmitThreads];          // exclusive prefix of the slices' range totals
     uint64_t range_base;
@@ -765,21 +770,27 @@ __device__ __forceinline__ void emit_stages(const StreamParams &P, StreamEmitSme
     const uint64_t seg0 = st0 * kConsumerWarps, seg1 = st1 * kConsumerWarps;
     uint64_t base = base0;
     const int64_t seg_pos0 = (int64_t)P.off - (int64_t)P.job.delta;
+    // the next batch's count words are loaded while this one is emitted
+    uint32_t word_next = seg0 + (uint64_t)t < seg1 ? P.seg_count[seg0 + (uint64_t)t] : 0u;
+    uint32_t par = 0u;
     for (uint64_t sb = seg0; sb < seg1; sb += kEmitThreads) {
-        const uint64_t seg = sb + (uint64_t)t;
-        const uint32_t word = seg < seg1 ? P.seg_count[seg] : 0u;
+        const uint32_t word = word_next;
+        const uint64_t segn = sb + kEmitThreads + (uint64_t)t;
+        word_next = segn < seg1 ? P.seg_count[segn] : 0u;
         const uint32_t c = word & kCountMask;
         const uint32_t inc = warp_incl_scan(c, lane);
-        if (lane == 31) S.scan_tmp[w] = inc;
+        // (a warp writes this parity's row again two batches later, after
+        // every warp has passed the next batch's barrier, so after its reads)
+        if (lane == 31) S.scan_tmp[par][w] = inc;
         __syncthreads();
         uint32_t wbase = 0u, btotal = 0u;
 #pragma unroll
         for (int k = 0; k < kEmitWarps; ++k) {
-            const uint32_t v = S.scan_tmp[k];
+            const uint32_t v = S.scan_tmp[par][k];
             if (k < w) wbase += v;
             btotal += v;
         }
-        __syncthreads();
+        par ^= 1u;
         const uint64_t excl = base + wbase + inc - c;
         const uint64_t first = sb + (uint64_t)w * 32u;
         const uint32_t todo = __ballot_sync(kFull, c != 0u && (word >> 16) == 0u);

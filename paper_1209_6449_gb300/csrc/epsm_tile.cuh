@@ -144,13 +144,9 @@ __device__ __noinline__ uint32_t exact_chunk_regs(const Pattern &pat, const uint
 // are all set; doubling shift-ANDs find those runs of m ones in log2 m steps.
 // A run of that byte in the text makes every start a candidate of the
 // fingerprint and code filters; this decides a chunk's 16 starts at once.
-template <int NW>
-__device__ __forceinline__ uint32_t run_starts16(const uint32_t (&R)[NW], uint32_t bb, uint32_t m) {
-    static_assert(NW <= 16, "a 64-bit byte mask");
-    uint64_t E = 0ull;
-#pragma unroll
-    for (int k = 0; k < NW; ++k) E |= (uint64_t)nibble_of(zero_bytes(R[k] ^ bb)) << (4 * k);
-    uint32_t L = 1u;  // bit i of E: bytes i .. i+L-1 all equal bb
+// Bits i (0..15) such that bits i .. i+m-1 of E are all set (1 <= m <= 48).
+__device__ __forceinline__ uint32_t runs_of(uint64_t E, uint32_t m) {
+    uint32_t L = 1u;  // bit i of E: bits i .. i+L-1 of the original all set
     while (2u * L <= m) {
         E &= E >> L;
         L *= 2u;
@@ -159,12 +155,59 @@ __device__ __forceinline__ uint32_t run_starts16(const uint32_t (&R)[NW], uint32
     return (uint32_t)E & 0xFFFFu;
 }
 
-// run_starts16 on the bytes of a chunk and the next chunk (m <= 17); out of
-// line, so the filter loop keeps its registers.
-__device__ __noinline__ uint32_t run_chunk_regs(const Pattern &pat, const uint4 cur, uint32_t n0,
-                                                uint32_t n1, uint32_t n2, uint32_t n3) {
-    const uint32_t R[8] = {cur.x, cur.y, cur.z, cur.w, n0, n1, n2, n3};
-    return run_starts16<8>(R, bcast_byte(pat.w[0], 0), pat.m);
+// Byte-equality mask of a chunk against the broadcast byte bb (bit k: byte k).
+__device__ __forceinline__ uint32_t eq_mask16(const uint4 c, uint32_t bb) {
+    return nibble_of(zero_bytes(c.x ^ bb)) | (nibble_of(zero_bytes(c.y ^ bb)) << 4) |
+           (nibble_of(zero_bytes(c.z ^ bb)) << 8) | (nibble_of(zero_bytes(c.w ^ bb)) << 12);
+}
+
+template <int NW>
+__device__ __forceinline__ uint32_t run_starts16(const uint32_t (&R)[NW], uint32_t bb, uint32_t m) {
+    static_assert(NW <= 16, "a 64-bit byte mask");
+    uint64_t E = 0ull;
+#pragma unroll
+    for (int k = 0; k < NW; ++k) E |= (uint64_t)nibble_of(zero_bytes(R[k] ^ bb)) << (4 * k);
+    return runs_of(E, m);
+}
+
+// The 16 bytes from the 16-byte aligned internal position pc, from the
+// staged bytes when they cover them, else from global memory (bytes outside
+// the text read as 0).
+__device__ __forceinline__ uint4 chunk_at(const SearchJob &J, int64_t pc, const StagedText &T) {
+    const int64_t o = pc - T.sbase;
+    if (T.inside && o >= 0 && o + 16 <= (int64_t)T.span) return *reinterpret_cast<const uint4 *>(T.buf + o);
+    const int64_t wa = pc >> 2;
+    uint4 c;
+    c.x = wa < 0 ? 0u : load_word(J, (uint64_t)wa);
+    c.y = wa + 1 < 0 ? 0u : load_word(J, (uint64_t)(wa + 1));
+    c.z = wa + 2 < 0 ? 0u : load_word(J, (uint64_t)(wa + 2));
+    c.w = wa + 3 < 0 ? 0u : load_word(J, (uint64_t)(wa + 3));
+    return c;
+}
+
+// Template argument MP of the strided block and 2-bit code variants' kernels
+// for a pattern of period 1 (one byte repeated): kernels of their own, so
+// that the period-1 test stays out of the ordinary filter loops.
+constexpr int kMpRun = 1;
+
+// The period-1 test of the strided block variant for a whole warp (starts
+// 16c - 15 .. 16c of each lane's chunk c, m <= 32): every lane takes the
+// byte-equality mask of its own chunk, the next chunk's comes from the next
+// lane and the previous chunk's from the lane before (lanes 31 and 0 read the
+// chunks past the step), so each chunk's bytes are compared once.  t0: the
+// lane's block is marked (a chunk without a marked block has no occurrence).
+__device__ __forceinline__ uint32_t run_block16(const SearchJob &J, const uint4 cur, int64_t p0,
+                                             const StagedText &T, uint32_t t0, int lane) {
+    const uint32_t bb = bcast_byte(J.pat.w[0], 0);
+    const uint32_t e_own = eq_mask16(cur, bb);
+    uint32_t e_next = __shfl_down_sync(kFull, e_own, 1);
+    uint32_t e_prev = __shfl_up_sync(kFull, e_own, 1);
+    // (p0 + 15 is the lane's chunk start, 16-byte aligned)
+    if (lane == 31) e_next = eq_mask16(chunk_at(J, p0 + 31, T), bb);
+    if (lane == 0) e_prev = eq_mask16(chunk_at(J, p0 - 1, T), bb);
+    // bit k of E: byte p0 - 1 + k; start p0 + i is bit i of E >> 1
+    const uint64_t E = (uint64_t)e_prev | ((uint64_t)e_own << 16) | ((uint64_t)e_next << 32);
+    return t0 ? runs_of(E >> 1, J.pat.m) : 0u;
 }
 
 // run_starts16 on the text from p0 (any alignment; m <= 32): 12 words from
@@ -576,6 +619,7 @@ __device__ __forceinline__ uint32_t chunk_hits(const SearchJob &J, const uint4 c
         // lookups of the plain block variant); starts 16c - 15 .. 16c.
         const uint32_t t0 = kSoundness ? 1u : table_bit(table, block_hash(cur.x, cur.y, pat.kbits));
         if (!__any_sync(kFull, t0 != 0u)) return 0u;
+        if constexpr (MP == kMpRun) return run_block16(J, cur, p0, T, t0, lane);
         return block_slow<V_BLOCK8S>(J, cur, p0, pblk, t0, 0u, T.buf, T.sbase, T.inside, T.tail,
                                      T.mtail);
     } else {
