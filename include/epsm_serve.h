@@ -7,7 +7,13 @@
  * wait in a queue; whenever one of `inflight` launch slots is free, every
  * queued query (up to `max_batch`) goes into one batched launch
  * (epsm_search_batch's kernel: queries on the same corpus share one pass over
- * it), so the work of consecutive batches overlaps on the device.  Texts
+ * it), so the work of consecutive batches overlaps on the device.  A batch of
+ * at most `small_batch` distinct queries runs as single searches instead, and
+ * in a larger batch the queries of m <= 4 on corpora of at least 16 MiB run
+ * as single searches after the batched launch, their positions placed after
+ * the batch's in the same output buffer (the direct compare such a query
+ * runs costs as much shared as alone, and a single search's pass is
+ * cheaper).  Texts
  * uploaded at run time are admitted against free device memory and an upload
  * budget, evicting the least recently used idle uploads first; their copies
  * run on a separate stream and overlap the searches.

@@ -379,7 +379,7 @@ uint64_t stages_for(uint64_t delta, uint64_t n, uint32_t m, int v) {
 epsm_status search_async_impl(epsm_ctx *c, int variant, const uint8_t *text, uint64_t n,
                               const uint8_t *pattern, uint32_t m, uint64_t *positions,
                               uint64_t capacity, uint64_t *count_dev, void *stream,
-                              int64_t pos_bias) {
+                              uint64_t *cursor) {
     if (!c || !pattern || !count_dev) return EPSM_ERR_ARG;
     if (m == 0 || m > EPSM_MAX_M_LONG) return EPSM_ERR_ARG;
     if (n > 0 && !text) return EPSM_ERR_ARG;
@@ -422,7 +422,7 @@ epsm_status search_async_impl(epsm_ctx *c, int variant, const uint8_t *text, uin
     p.chunk_full0 = (p.job.delta + 15u) / 16u;
     p.chunk_full1 = p.job.lim / 16u;
     p.emit = capacity > 0 ? 1 : 0;
-    (void)pos_bias;
+    p.cursor = cursor;
     if ((st = ensure_stream_scratch(c, p.nstages, s)) != EPSM_OK) return st;
     p.positions = positions;
     p.capacity = capacity;
@@ -995,7 +995,7 @@ EPSM_API epsm_status epsm_search_async(epsm_ctx *c, const uint8_t *text, uint64_
     DeviceGuard dg(c->device);
     if (!dg.ok) return EPSM_ERR_CUDA;
     return search_async_impl(c, EPSM_VARIANT_AUTO, text, n, pattern, m, positions, capacity,
-                             count_dev, stream, 0);
+                             count_dev, stream, nullptr);
 }
 
 EPSM_API epsm_status epsm_search_variant(epsm_ctx *c, int variant, const uint8_t *text,
@@ -1006,7 +1006,7 @@ EPSM_API epsm_status epsm_search_variant(epsm_ctx *c, int variant, const uint8_t
     DeviceGuard dg(c->device);
     if (!dg.ok) return EPSM_ERR_CUDA;
     return search_async_impl(c, variant, text, n, pattern, m, positions, capacity, count_dev,
-                             stream, 0);
+                             stream, nullptr);
 }
 
 EPSM_API epsm_status epsm_search(epsm_ctx *c, const uint8_t *text, uint64_t n,
@@ -1016,7 +1016,7 @@ EPSM_API epsm_status epsm_search(epsm_ctx *c, const uint8_t *text, uint64_t n,
     DeviceGuard dg(c->device);
     if (!dg.ok) return EPSM_ERR_CUDA;
     epsm_status st = search_async_impl(c, EPSM_VARIANT_AUTO, text, n, pattern, m, positions,
-                                       capacity, &c->misc->count, stream, 0);
+                                       capacity, &c->misc->count, stream, nullptr);
     if (st != EPSM_OK) return st;
     uint32_t err = 0;
     if ((st = read_misc(c, pick_stream(c, stream), &err)) != EPSM_OK) return st;
@@ -1136,7 +1136,7 @@ EPSM_API epsm_status epsm_search_host(epsm_ctx *c, const uint8_t *text_host, uin
         offsets_host[k] = off;
         const uint64_t room = off < capacity ? capacity - off : 0;
         st = search_async_impl(c, EPSM_VARIANT_AUTO, c->dtext, n, patterns_host + p0, ms[k],
-                               room ? c->dpos + off : nullptr, room, &c->misc->count, s, 0);
+                               room ? c->dpos + off : nullptr, room, &c->misc->count, s, nullptr);
         if (st != EPSM_OK) return st;
         uint32_t err = 0;
         if ((st = read_misc(c, s, &err)) != EPSM_OK) return st;

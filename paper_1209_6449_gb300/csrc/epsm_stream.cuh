@@ -169,6 +169,9 @@ struct StreamParams {
     int emit;              // 0: count only
     const uint8_t *tail;   // long pattern (m > 32, block variant): its bytes past the first 32
     uint32_t mtail;        // their number (0: none)
+    uint64_t *cursor;      // device word: output index of the first position (null: 0); the
+                           // emission kernel advances it by the count (searches chained
+                           // into one buffer)
 };
 
 // Chunk c of job J as staged in `buf` (the stage's first chunk is c0), or read
@@ -887,6 +890,9 @@ __global__ void __launch_bounds__(stream::kEmitThreads, EPSM_EMIT_MIN_BLOCKS)
     const uint32_t nr = P.nranges;
     const uint32_t per = (nr + kEmitThreads - 1) / kEmitThreads;
     const uint64_t *rt = reinterpret_cast<const uint64_t *>(P.range_total);
+    // (read by every block before the last one to finish advances it)
+    const uint64_t cbase = P.cursor ? *P.cursor : 0ull;
+    uint64_t all = 0;
     {
         const uint32_t r0 = (uint32_t)t * per, r1 = r0 + per < nr ? r0 + per : nr;
         uint64_t sum = 0;
@@ -900,7 +906,7 @@ __global__ void __launch_bounds__(stream::kEmitThreads, EPSM_EMIT_MIN_BLOCKS)
         }
         if (lane == 31) S.scan64[warp] = inc;
         __syncthreads();
-        uint64_t before = 0, all = 0;
+        uint64_t before = 0;
 #pragma unroll
         for (int k = 0; k < kEmitWarps; ++k) {
             const uint64_t v = S.scan64[k];
@@ -921,7 +927,7 @@ __global__ void __launch_bounds__(stream::kEmitThreads, EPSM_EMIT_MIN_BLOCKS)
             uint64_t part = 0;
             for (uint32_t q = sl * per + (uint32_t)lane; q < r; q += 32) part += rt[q];
             part = warp_sum64(part);
-            if (lane == 0) S.range_base = S.slice_pre[sl] + part;
+            if (lane == 0) S.range_base = cbase + S.slice_pre[sl] + part;
         }
         __syncthreads();
         const uint64_t st0 = (uint64_t)r * P.range_stages;
@@ -940,6 +946,7 @@ __global__ void __launch_bounds__(stream::kEmitThreads, EPSM_EMIT_MIN_BLOCKS)
         if (t == 0) {
             P.misc->ticket2 = 0u;
             P.misc->done2 = 0u;
+            if (P.cursor) *P.cursor = cbase + all;
         }
         __threadfence();
     }

@@ -123,6 +123,39 @@ def test_dense_queries_grow_the_output(corpora, torch):
         srv.close()
 
 
+@pytest.mark.parametrize("out_capacity", [1 << 12, 1 << 26])
+def test_short_queries_on_large_corpora_follow_the_batch(torch, out_capacity):
+    """On corpora of at least 16 MiB, a batch's short queries (m <= 4) run as
+    single searches whose positions follow the batched part's in the same
+    buffer; with a small buffer the whole mixed batch overflows and is re-run.
+    Every result equals the oracle's, duplicates included."""
+    import paper_1209_6449_gb300 as epsm
+    big = []
+    for i, k in enumerate(("dna", "protein")):
+        spec = gen.TextSpec(k, 90 + i)
+        host = spec.host((20 << 20) + 7 * i)
+        big.append((spec, host, torch.from_numpy(host).cuda()))
+    rng = np.random.default_rng(21)
+    qs = []
+    for k in range(60):
+        c = k % 2
+        m = int(rng.integers(1, 5)) if k % 3 else int(rng.integers(5, 33))
+        spec, host, _ = big[c]
+        p = (gen.planted_patterns(spec, host.size, m, 1, stream_seed=k)[0] if k % 2
+             else gen.random_patterns(spec, m, 1, stream_seed=k)[0])
+        qs.append((c, p))
+    qs += qs[:6]  # the same queries again in the batch
+    srv = epsm.Server(0, max_batch=128, inflight=1, out_capacity=out_capacity)
+    try:
+        req, got = _serve_all(srv, big, qs, torch)
+        for rid, (c, p) in req.items():
+            assert np.array_equal(got[rid], oracle.search(big[c][1], p, threads=8)), (c, p)
+        if out_capacity < 1 << 20:
+            assert srv.stats()["reruns"] >= 1
+    finally:
+        srv.close()
+
+
 def test_upload_admission_and_eviction(corpora, torch):
     import paper_1209_6449_gb300 as epsm
     n = 1 << 20
