@@ -9,11 +9,12 @@
  * (epsm_search_batch's kernel: queries on the same corpus share one pass over
  * it), so the work of consecutive batches overlaps on the device.  A batch of
  * at most `small_batch` distinct queries runs as single searches instead, and
- * in a larger batch the queries of m <= 4 on corpora of at least 16 MiB run
- * as single searches after the batched launch, their positions placed after
- * the batch's in the same output buffer (the direct compare such a query
- * runs costs as much shared as alone, and a single search's pass is
- * cheaper).  Texts
+ * in a larger batch the queries of m <= 4 on corpora of at least 16 MiB (of
+ * m <= 10 when the batch's patterns on that corpus use at most 4 distinct
+ * bytes) run as single searches after the batched launch, their positions
+ * placed after the batch's in the same output buffer (such queries cost as
+ * much in the shared pass as alone, and a single search's pass is cheaper).
+ * Texts
  * uploaded at run time are admitted against free device memory and an upload
  * budget, evicting the least recently used idle uploads first; their copies
  * run on a separate stream and overlap the searches.
