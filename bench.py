@@ -93,6 +93,11 @@ def parse():
                     help="arrival window per rate for the serving engine")
     ap.add_argument("--serve-pq-secs", type=float, default=0.25,
                     help="arrival window per rate for the per-query path (it saturates early)")
+    ap.add_argument("--served-only", action="store_true",
+                    help="run the served workload alone and print its JSON (the main run starts "
+                         "it this way, in a child process with a time limit)")
+    ap.add_argument("--serve-timeout", type=float, default=300.0,
+                    help="seconds the served workload's child process may take")
     return ap.parse_args()
 
 
@@ -680,6 +685,21 @@ def run_batched(ctx, torch, npairs):
                       "download) vs one asynchronous launch per pair and a final synchronize"}
 
 
+def run_served_child(args):
+    """The served workload in a child process with a time limit, so that a
+    stalled serving engine cannot hold up the rest of the report."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--served-only", "--serve-rates", args.serve_rates,
+           "--serve-secs", str(args.serve_secs), "--serve-pq-secs", str(args.serve_pq_secs)]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=args.serve_timeout)
+    except subprocess.TimeoutExpired:
+        return {"unavailable": f"served workload did not finish within {args.serve_timeout:.0f} s"}
+    lines = [x for x in r.stdout.strip().splitlines() if x.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return {"unavailable": f"served workload failed (exit {r.returncode}): {r.stderr.strip()[-300:]}"}
+    return json.loads(lines[-1])
+
+
 def run_served(torch, args):
     """The served workload: 4 corpora of 1 GiB resident in HBM (sigma 4, 20,
     64 Zipf, 96-symbol order-2 Markov), a Poisson stream of queries (corpus
@@ -767,6 +787,11 @@ def main():
         return run_reference(args)
     if args.case:
         return run_case(args)
+    if args.served_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(run_served(torch, args)), flush=True)
+        return 0
     if args.sample:
         return run_sample(args)
 
@@ -842,7 +867,7 @@ def main():
     served = None
     if not args.no_serve and world == 1:
         torch.cuda.empty_cache()
-        served = run_served(torch, args)
+        served = run_served_child(args)
 
     if rank == 0:
         line = {"metric": metric, "value": round(value, 2), "unit": UNIT, "n_gpus": world,

@@ -575,13 +575,15 @@ __device__ __noinline__ void walk_chains(Smem &S, int w, uint4 cur, uint32_t n0,
                 const uint2 E = S.tab.ent[e];
                 const uint32_t meta = E.y;
                 const uint32_t i = meta >> 17, j = (meta >> 11) & 7u, K = 1u << ((meta >> 14) & 3u);
-                if (((meta >> 16) & 1u) == w4 && E.x == lo && (q & (K - 1u)) == 0u && j <= q &&
-                    q - j <= 15u) {
-                    const uint32_t b = q - j;
+                // start 16c + q - j: in this chunk, or (q = 0) in the one
+                // before, when that one is in the warp's segment
+                const int b = (int)q - (int)j;
+                if (((meta >> 16) & 1u) == w4 && E.x == lo && (q & (K - 1u)) == 0u && b <= 15 &&
+                    (b >= 0 || chunk > 0u)) {
                     const int64_t Pp = p0 + (int64_t)b;
                     const uint32_t m = S.tab.m[i];
                     if (Pp >= V.delta && Pp <= V.lim - (int64_t)m && verify_at(V.gpw + 8u * i, m, Pp, V))
-                        push_hit(S, w, i, chunk, b);
+                        push_hit(S, w, i, b >= 0 ? chunk : chunk - 1u, (uint32_t)(b & 15));
                 }
                 const uint32_t next = meta & kEndChain;
                 if (next == kEndChain) break;
@@ -591,19 +593,22 @@ __device__ __noinline__ void walk_chains(Smem &S, int w, uint4 cur, uint32_t n0,
     }
 }
 
-// Lookups of one chunk: 8-byte windows at q = 0, K8, 2 K8, .., 16 and 4-byte
-// windows at q = 0, K4, .., 16 (K = 0: no window of that width; every
-// stride is at least 2, so q = 16 is always looked up).  A window passes
-// when its head slot is non-empty and carries its tag or tag 0; the chains of
-// the passing windows are walked afterwards.
+// Lookups of one chunk: 8-byte windows at q = 0, K8, 2 K8, .. < 16 and 4-byte
+// windows at q = 0, K4, .. < 16 (K = 0: no window of that width); a window at
+// 16c + q holds the starts 16c + q - j (j < K), so the window at q = 0 also
+// serves the chunk before, and only the segment's last chunk (`last`) looks
+// up the window at q = 16, the next segment's first.  A window passes when
+// its head slot is non-empty and carries its tag or tag 0; the chains of the
+// passing windows are walked afterwards.
 template <int K8, int K4>
 __device__ __forceinline__ void filter_chunk(Smem &S, int w, uint4 cur, uint32_t n0, uint32_t n1,
-                                             int64_t p0, uint32_t chunk) {
+                                             int64_t p0, uint32_t chunk, bool last) {
     const uint32_t R[6] = {cur.x, cur.y, cur.z, cur.w, n0, n1};
     const uint32_t *head = S.tab.head;
     uint32_t need8 = 0u, need4 = 0u;
 #pragma unroll
     for (int q = 0; q <= 16; ++q) {
+        if (q == 16 && !last) break;
         const int k = q >> 2, j = q & 3;
         const uint32_t lo = j ? __funnelshift_r(R[k], R[k + 1], 8 * j) : R[k];
         if constexpr (K8 != 0) {
@@ -748,7 +753,7 @@ __device__ __noinline__ void shared_filter(const Params &P, const Header &H, con
         const uint32_t n0 = __shfl_sync(kFull, nsrc.x, src);
         const uint32_t n1 = __shfl_sync(kFull, nsrc.y, src);
         filter_chunk<K8, K4>(S, w, cur, n0, n1, sp0 + (int64_t)((32 * u + lane) * 16),
-                             (uint32_t)(32 * u + lane));
+                             (uint32_t)(32 * u + lane), u == 3 && lane == 31);
     }
     __syncwarp();
     finish_shared(P, H, G, S, ls, w, lane);
