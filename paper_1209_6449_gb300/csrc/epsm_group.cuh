@@ -11,16 +11,17 @@
 // at a multiple of K in [s, s+K), at j = that start - s, so looking up the
 // text windows at the multiples of K finds each occurrence exactly once.  A
 // lane holding chunk c (starts 16c .. 16c+15) looks up the windows at 16c + q
-// for q = 0..16, q a multiple of the group's smallest stride of that width,
-// and accepts an entry (i, j, K) when K divides q and 0 <= q - j <= 15, so
-// the start falls in its own chunk.
+// for q = 0 .. < 16, q a multiple of the group's smallest stride of that
+// width, and accepts an entry (i, j, K) when K divides q; the start q - j
+// falls in its own chunk or, for q = 0, in the chunk before (the segment's
+// last chunk also looks up q = 16, for its own starts).
 // The table lives in shared memory: 4096 head slots, each 0 or a 16-bit tag
-// of the window's hash plus the index of its first entry (tag 0 marks a slot
-// shared by several entries), and the entries {window, pattern, j, K, next}.
-// A window whose slot is empty or carries another tag is rejected with one
-// shared load; the chains of the others are compared exactly after the
-// chunk's lookups and a window match is checked in full (from the staged
-// bytes where they cover it).
+// of the window's hash plus the index of its first entry (for a slot shared
+// by several entries, the OR of their tags), and the entries {window,
+// pattern, j, K, next}.  A window whose slot is empty or whose tag has a bit
+// outside the slot's is rejected with one shared load; the chains of the
+// others are compared exactly after the chunk's lookups and a window match is
+// checked in full (from the staged bytes where they cover it).
 //
 // Confirmed hits go to a per-warp list; each pattern's segment count and masks
 // are then written in the layout of the single search (one segment numbering
@@ -111,7 +112,7 @@ struct Header {
 // 8-byte window is compared on its first 4 bytes after its 16-bit tag matched;
 // the full check decides.
 struct SharedTable {
-    uint32_t head[kSlots];           // 0, or tag << 16 | (entry + 1); tag 0: several entries
+    uint32_t head[kSlots];           // 0, or (OR of its entries' tags) << 16 | (entry + 1)
     uint2 ent[kMaxEnt];
     uint64_t stage0[kMaxShared];     // per-pattern stage numbering
     uint32_t nst[kMaxShared];
@@ -131,6 +132,7 @@ static_assert(sizeof(SharedTable) % 16 == 0, "copied as uint4");
 struct GroupTables {
     SharedTable t;
     uint32_t pw[kMaxShared][8];
+    uint32_t sig[kSlots];            // (table build) per slot: OR of its entries' tags
 };
 
 struct Params {
@@ -211,6 +213,15 @@ __device__ __forceinline__ uint32_t slot_of(uint32_t x) { return x >> (32 - kSlo
 
 __device__ __forceinline__ uint32_t tag_of(uint32_t x) { return ((x >> 4) & 0xFFFFu) | 1u; }
 
+// A slot's head keeps the OR of its entries' tags (the one tag when it holds
+// one entry); a window passes when its tag's bits are all among them, so a
+// window that merely shares a crowded slot mostly skips the chain walk (one
+// AND and one compare, as for a single tag).
+__device__ __forceinline__ bool slot_passes(uint32_t v, uint32_t x) {
+    const uint32_t t = tag_of(x);
+    return v != 0u && ((v >> 16) & t) == t;
+}
+
 // ---------------------------------------------------------------------------
 // pattern preprocessing (a kernel): block-variant tables of individual
 // patterns and the groups' shared tables
@@ -256,7 +267,11 @@ __global__ void build_group_tables_kernel(const Params P) {
         if (G.comb == kNone) continue;
         SharedTable &T = P.comb[G.comb].t;  // (groups of more than one pattern)
         uint32_t (*tpw)[8] = P.comb[G.comb].pw;
-        for (int i = threadIdx.x; i < kSlots; i += blockDim.x) T.head[i] = 0u;
+        uint32_t *sig = P.comb[G.comb].sig;
+        for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
+            T.head[i] = 0u;
+            sig[i] = 0u;
+        }
         for (uint32_t i = threadIdx.x; i < G.nshared; i += blockDim.x) {
             const JobDesc &D = P.jobs[H.group_jobs[G.job0 + i]];
 #pragma unroll
@@ -288,14 +303,15 @@ __global__ void build_group_tables_kernel(const Params P) {
             const uint32_t lk = (uint32_t)(__ffs((int)D.kstride) - 1);
             const uint32_t e = D.ent0 + j;
             const uint32_t old = atomicExch(&T.head[slot_of(x)], (tag_of(x) << 16) | (e + 1u));
+            atomicOr(&sig[slot_of(x)], tag_of(x));
             const uint32_t next = old ? (old & 0xFFFFu) - 1u : kEndChain;
             T.ent[e] = make_uint2(lo, next | (j << 11) | (lk << 14) | ((w4 ? 1u : 0u) << 16) | (i << 17));
         }
         __syncthreads();
-        // a slot holding a chain of several entries gets tag 0 (always walk it)
+        // a slot holding a chain of several entries gets the OR of their tags
         for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
             const uint32_t v = T.head[i];
-            if (v && (T.ent[(v & 0xFFFFu) - 1u].y & kEndChain) != kEndChain) T.head[i] = v & 0xFFFFu;
+            if (v) T.head[i] = (sig[i] << 16) | (v & 0xFFFFu);
         }
         __syncthreads();
     }
@@ -598,8 +614,8 @@ __device__ __noinline__ void walk_chains(Smem &S, int w, uint4 cur, uint32_t n0,
 // 16c + q holds the starts 16c + q - j (j < K), so the window at q = 0 also
 // serves the chunk before, and only the segment's last chunk (`last`) looks
 // up the window at q = 16, the next segment's first.  A window passes when
-// its head slot is non-empty and carries its tag or tag 0; the chains of the
-// passing windows are walked afterwards.
+// its head slot is non-empty and holds all of its tag's bits; the chains of
+// the passing windows are walked afterwards.
 template <int K8, int K4>
 __device__ __forceinline__ void filter_chunk(Smem &S, int w, uint4 cur, uint32_t n0, uint32_t n1,
                                              int64_t p0, uint32_t chunk, bool last) {
@@ -615,17 +631,13 @@ __device__ __forceinline__ void filter_chunk(Smem &S, int w, uint4 cur, uint32_t
             if (q % K8 == 0) {
                 const uint32_t hi = q == 16 ? R[5] : (j ? __funnelshift_r(R[k + 1], R[k + 2 < 6 ? k + 2 : 5], 8 * j) : R[k + 1]);
                 const uint32_t x = hash8(lo, hi);
-                const uint32_t v = head[slot_of(x)];
-                const uint32_t t = v >> 16;
-                if (v && (t == tag_of(x) || t == 0u)) need8 |= 1u << q;
+                if (slot_passes(head[slot_of(x)], x)) need8 |= 1u << q;
             }
         }
         if constexpr (K4 != 0) {
             if (q % K4 == 0) {
                 const uint32_t x = hash4(lo);
-                const uint32_t v = head[slot_of(x)];
-                const uint32_t t = v >> 16;
-                if (v && (t == tag_of(x) || t == 0u)) need4 |= 1u << q;
+                if (slot_passes(head[slot_of(x)], x)) need4 |= 1u << q;
             }
         }
     }
