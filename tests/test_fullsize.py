@@ -12,6 +12,8 @@ stand-ins.
   i.i.d. pattern per text and m);
 - a 4.5 GiB text, so that positions pass 2^32, compared start window by start
   window over the whole text;
+- the large scan's 16 GiB texts in the benchmark's configuration (alphabet
+  class tuning, the scan's own patterns), compared the same way;
 - the full batched workload (8192 uneven pairs, about 24 GiB of text), each
   pair against the oracle on that pair alone;
 - the served workload's four 1 GiB corpora, each served query against the
@@ -170,6 +172,39 @@ def test_text_past_four_gib(ctx, torch):
             assert got.size and int(got[-1]) >= (1 << 32)
         _windowed_compare(host, p, got)
         assert ctx.count(text, p) == cnt
+    del buf, text
+
+
+# the large scan's texts, their alphabet classes and a subset of its searches
+# (m, pattern kind): dense and sparse outputs, every filter family, and the
+# period-1 kernels on the runs text
+SCAN_CASES = {"dna": ("dna", [(2, "planted"), (8, "iid"), (32, "planted")]),
+              "markov96": ("text", [(4, "planted"), (16, "iid")]),
+              "dna_runs": ("dna", [(3, "runs"), (8, "runs"), (24, "runs")])}
+
+
+@pytest.mark.parametrize("kind", list(SCAN_CASES))
+def test_large_scan_texts_in_the_timed_configuration(torch, epsm, kind):
+    """The 16 GiB texts of the large scan (seed 0), searched as the benchmark
+    does (a context with its alphabet class's tuning rows, the scan's own
+    patterns), every position compared with the oracle start window by start
+    window over the whole text."""
+    n = 16 * GiB
+    cls, cases = SCAN_CASES[kind]
+    spec = gen.TextSpec(kind, 0)
+    host = spec.host_parallel(n)
+    buf, text = _device_text(torch, spec, n)
+    c = epsm.Context(0, text_class=cls)
+    try:
+        for m, mode in cases:
+            p = (b"A" * m if mode == "runs" else gen.random_patterns(spec, m, 1)[0] if mode == "iid"
+                 else gen.planted_patterns(spec, n, m, 1)[0])
+            cnt = c.count(text, p)
+            _, got = _gpu_positions(c, text, p, cnt + 8)
+            assert got.size == cnt
+            _windowed_compare(host, p, got, window=1 * GiB)
+    finally:
+        c.close()
     del buf, text
 
 
