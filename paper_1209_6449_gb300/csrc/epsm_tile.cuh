@@ -494,6 +494,19 @@ __device__ __forceinline__ bool block4_any(const uint4 cur, uint32_t n0, uint32_
            (cur.w == q1) | (cur.w == q2) | (cur.w == q3) | (n0 == q1) | (n0 == q2) | (n0 == q3);
 }
 
+// The 16 byte flags of four zero_bytes() words (bit 7 of each byte) as a
+// 16-bit mask, bit 4k + b for byte b of word k.  Words k and k + 1 share one
+// 32 x 32 -> 64-bit multiply: with word k's flags moved to bits 8b and word
+// k + 1's to bits 8b + 4, the constant's term 2^(28 - 7b) carries byte b's two
+// flags to bits 28 + b and 32 + b, and no two partial products meet, so the
+// product's bits 28..35 are the two words' nibbles (half the shifts and ORs
+// of packing each word alone, and the multiplies run on the FMA pipe).
+__device__ __forceinline__ uint32_t pack_flags4(uint32_t z0, uint32_t z1, uint32_t z2, uint32_t z3) {
+    const uint64_t a = (uint64_t)((z0 >> 7) | (z1 >> 3)) * 0x10204080ull;
+    const uint64_t b = (uint64_t)((z2 >> 7) | (z3 >> 3)) * 0x10204080ull;
+    return ((uint32_t)(a >> 28) & 0xFFu) | (((uint32_t)(b >> 28) & 0xFFu) << 8);
+}
+
 // Hit mask of one chunk (before start-validity masking).
 //   cur    the chunk's words; nsrc: this lane's contribution to the neighbour
 //   shuffle (the chunk the lane before needs as "next chunk").
@@ -530,10 +543,7 @@ __device__ __forceinline__ uint32_t chunk_hits(const SearchJob &J, const uint4 c
         }
         // most chunks of a large alphabet have no match: skip the packing
         if ((z[0] | z[1] | z[2] | z[3]) == 0u) return 0u;
-        uint32_t h = 0u;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) h |= nibble_of(z[k]) << (4 * k);
-        return h;
+        return pack_flags4(z[0], z[1], z[2], z[3]);
     } else if constexpr (kSoundness && (V == V_PREFIX4 || V == V_PREFIX8 || V == V_BLOCK4)) {
         // soundness build: every start is a candidate, checked in full
         const uint32_t n0 = __shfl_sync(kFull, nsrc.x, src);
