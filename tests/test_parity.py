@@ -142,6 +142,30 @@ def test_high_bytes_and_zero_bytes(ctx, torch):
             _check(ctx, torch, host, p, 0, offset=m % 16)
 
 
+@pytest.mark.parametrize("variant", [6, 8])
+def test_period_one_kernels_at_text_edges(ctx, torch, variant):
+    """The period-1 kernels of the code and strided block variants read the
+    chunks around a lane's own (bytes outside the text read as 0): a text of
+    one byte value searched with that byte repeated, 0x00 included, at ragged
+    lengths and alignments, must give exactly the n - m + 1 starts (closed
+    form), and a single other byte must remove exactly the starts covering
+    it."""
+    for byte in (0x00, 0x41, 0xFF):
+        for m in (min(VARIANTS[variant]), 9, max(VARIANTS[variant])):
+            if m not in VARIANTS[variant]:
+                continue
+            for n in (m, m + 1, 511, 2 * TILE + 7, 3 * TILE + 1):
+                for offset in (0, 1, 15):
+                    host = np.full(n + offset, byte, dtype=np.uint8)
+                    dev = torch.from_numpy(host).cuda()[offset:]
+                    cnt, pos = ctx.search(dev, bytes([byte]) * m, capacity=n + 8, variant=variant)
+                    assert cnt == n - m + 1, (byte, m, n, offset, cnt)
+                    assert np.array_equal(pos.cpu().numpy(), np.arange(n - m + 1))
+                    if n > 2 * m:
+                        host[offset + n // 2] ^= 0x5A  # one other byte in the middle
+                        _check(ctx, torch, host, bytes([byte]) * m, variant, offset=offset)
+
+
 def test_capacity_overflow_and_count_only(ctx, torch, epsm):
     host = np.full(50_000, ord("c"), dtype=np.uint8)
     dev = torch.from_numpy(host).cuda()
