@@ -202,9 +202,12 @@ __device__ __forceinline__ uint32_t run_block16(const SearchJob &J, const uint4 
     const uint32_t e_own = eq_mask16(cur, bb);
     uint32_t e_next = __shfl_down_sync(kFull, e_own, 1);
     uint32_t e_prev = __shfl_up_sync(kFull, e_own, 1);
-    // (p0 + 15 is the lane's chunk start, 16-byte aligned)
-    if (lane == 31) e_next = eq_mask16(chunk_at(J, p0 + 31, T), bb);
-    if (lane == 0) e_prev = eq_mask16(chunk_at(J, p0 - 1, T), bb);
+    // lanes 0 and 31 read the chunk before and the chunk after the step in
+    // one code path (p0 + 15 is the lane's chunk start, 16-byte aligned)
+    if (lane == 0 || lane == 31) {
+        const uint32_t e_edge = eq_mask16(chunk_at(J, lane == 0 ? p0 - 1 : p0 + 31, T), bb);
+        if (lane == 0) e_prev = e_edge; else e_next = e_edge;
+    }
     // bit k of E: byte p0 - 1 + k; start p0 + i is bit i of E >> 1
     const uint64_t E = (uint64_t)e_prev | ((uint64_t)e_own << 16) | ((uint64_t)e_next << 32);
     return t0 ? runs_of(E >> 1, J.pat.m) : 0u;
